@@ -1,0 +1,791 @@
+/*
+ * mpcd_oracle.c -- plain CPU oracle for the SRD step (test infrastructure).
+ *
+ * Written for a reader holding the paper (arXiv:1801.10187) beside it: every
+ * stage is a straight loop over particles or cells, in the paper's order
+ * (Sec. 3, step flow: stream, bin, cell properties, collide).  No sorting, no
+ * blocking, no fusion.  Compiled with -O2 -ffp-contract=off so that no
+ * multiply-add is fused except where fma()/fmaf() is written out.
+ *
+ * Only the test suite, the smoke check and the benchmark's CPU baseline use
+ * this file; the GPU path shares no code with it.
+ */
+#include "mpcd_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC11:  */
+/* "Parallel random numbers: as easy as 1, 2, 3").  Ten rounds; each round   */
+/* multiplies counter words 0 and 2 by two fixed odd constants, mixes the    */
+/* high halves with the other words and the key; the key advances by two     */
+/* Weyl constants between rounds.  The paper (Sec. 3.6) uses a hash-based    */
+/* generator seeded by (cell, timestep, seed); Philox plays that role here.  */
+/* ------------------------------------------------------------------------ */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u; /* golden-ratio Weyl increment */
+      k1 += 0xBB67AE85u; /* sqrt(3)-1 Weyl increment    */
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t y0 = hi1 ^ x1 ^ k0;
+    uint32_t y1 = lo1;
+    uint32_t y2 = hi0 ^ x3 ^ k1;
+    uint32_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* One draw: counter (c0, c1, t_lo, t_hi), key (seed_lo, seed_hi ^ purpose). */
+static void draw4(uint64_t seed, uint32_t purpose, uint32_t c0, uint32_t c1, uint64_t t,
+                  uint32_t w[4]) {
+  uint32_t ctr[4] = {c0, c1, (uint32_t)t, (uint32_t)(t >> 32)};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ purpose};
+  oracle_philox4x32_10(ctr, key, w);
+}
+
+/* Uniform double in [0,1): top 53 bits of the 64-bit word (hi, lo). */
+static double u01_53(uint32_t hi, uint32_t lo) {
+  uint64_t x = ((uint64_t)hi << 32) | (uint64_t)lo;
+  return (double)(x >> 11) * 0x1p-53;
+}
+
+static const double TWO_PI = 6.283185307179586;
+
+/* cos and sin of 2 pi w / 2^32 in float: the top two bits of w pick the
+ * quadrant (an exact swap/negation), the other 30 bits give the angle in
+ * [0, pi/2), so the float argument carries no large-angle rounding. */
+static void cos_sin_turn_f(uint32_t w, float* c, float* s) {
+  uint32_t q = w >> 30;
+  float f = (float)(w & 0x3FFFFFFFu) * 0x1p-30f;
+  float th = f * 1.57079637f;
+  float ct = cosf(th), st = sinf(th);
+  if (q == 0) { *c = ct; *s = st; }
+  else if (q == 1) { *c = -st; *s = ct; }
+  else if (q == 2) { *c = -ct; *s = -st; }
+  else { *c = st; *s = -ct; }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2 / Sec. 3.4: random grid shift, one vector per step.  Quantised to  */
+/* 2^-32 (cell edge a = 1) so that floor(x - s) is exact in double.          */
+/* ------------------------------------------------------------------------ */
+void oracle_shift(uint64_t seed, uint64_t t, double s[3]) {
+  uint32_t w[4];
+  draw4(seed, ORACLE_PURPOSE_SHIFT, 0xFFFFFFFFu, 0u, t, w);
+  for (int k = 0; k < 3; ++k) {
+    int64_t S = (int64_t)w[k] - (int64_t)2147483648LL;
+    s[k] = (double)S * 0x1p-32;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.6: rotation axis uniform on the unit sphere by cylindrical          */
+/* projection: z uniform in [-1,1), phi uniform in [0, 2 pi).                 */
+/* ------------------------------------------------------------------------ */
+void oracle_axis(uint64_t seed, uint64_t t, uint32_t cell, int32_t precision, double n[3]) {
+  uint32_t w[4];
+  draw4(seed, ORACLE_PURPOSE_ROT, cell, 0u, t, w);
+  /* z = 2u - 1 and sqrt(1 - z^2) = 2 sqrt(u (1 - u)) with u = w0 / 2^32, so
+   * that 1 - u is exact and the pole region keeps full relative precision. */
+  if (precision == ORACLE_MIXED) {
+    float a = (float)w[0] * 0x1p-32f;
+    float b = (float)(4294967296LL - (int64_t)w[0]) * 0x1p-32f;
+    float z = (float)(2LL * (int64_t)w[0] - 4294967296LL) * 0x1p-32f;
+    float r = 2.0f * sqrtf(a * b);
+    float cphi, sphi;
+    cos_sin_turn_f(w[1], &cphi, &sphi);
+    n[0] = (double)(r * cphi);
+    n[1] = (double)(r * sphi);
+    n[2] = (double)z;
+  } else {
+    double a = (double)w[0] * 0x1p-32;
+    double b = (double)(4294967296LL - (int64_t)w[0]) * 0x1p-32;
+    double z = a - b;
+    double r = 2.0 * sqrt(a * b);
+    double phi = TWO_PI * ((double)w[1] * 0x1p-32);
+    n[0] = r * cos(phi);
+    n[1] = r * sin(phi);
+    n[2] = z;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2 Eq. (thermo) and Sec. 3.6: kinetic energy of a cell relative to    */
+/* its centre of mass drawn from the Maxwell-Boltzmann distribution for      */
+/* 3(Nc-1) degrees of freedom, i.e. Gamma(shape 3(Nc-1)/2, scale kT), by     */
+/* Marsaglia & Tsang (2000) with a Box-Muller normal (cosine branch).        */
+/* Attempt j uses counters (cell, 1+2j) and (cell, 2+2j).                     */
+/* ------------------------------------------------------------------------ */
+int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, double kT,
+                          int32_t precision, double* ehat) {
+  if (nc < 2) return -1;
+  if (precision == ORACLE_MIXED) {
+    float kk = 1.5f * (float)(nc - 1);
+    float d = kk - 1.0f / 3.0f;
+    float c = 1.0f / sqrtf(9.0f * d);
+    double dd = (double)d, cd = (double)c;
+    float kTf = (float)kT;
+    for (uint32_t j = 0; j < 64; ++j) {
+      uint32_t wa[4], wb[4];
+      draw4(seed, ORACLE_PURPOSE_THERMO, cell, 1u + 2u * j, t, wa);
+      draw4(seed, ORACLE_PURPOSE_THERMO, cell, 2u + 2u * j, t, wb);
+      /* 1 - U1 from the exact integer 2^32 - w, cos(2 pi U2) by quadrants,
+       * U3 = w / 2^32: the high words of the double-precision uniforms. */
+      float e1 = (float)(4294967296LL - (int64_t)wa[0]) * 0x1p-32f;
+      float U3 = (float)wb[0] * 0x1p-32f;
+      float c2, s2;
+      cos_sin_turn_f(wa[2], &c2, &s2);
+      float x = sqrtf(-2.0f * logf(e1)) * c2;
+      float t1 = 1.0f + c * x;
+      if (!(t1 > 0.0f)) continue;
+      float v = t1 * t1 * t1;
+      float lhs = logf(U3);
+      float rhs = 0.5f * (x * x) + d - d * v + d * logf(v);
+      float diff = lhs - rhs;
+      int accept;
+      if (fabsf(diff) > 1e-3f * (1.0f + d)) {
+        accept = diff < 0.0f;
+      } else {
+        /* Too close to the acceptance boundary for float rounding to decide:
+         * decide in double from the same uniforms. */
+        double xd = sqrt(-2.0 * log((double)e1)) * cos(TWO_PI * ((double)wa[2] * 0x1p-32));
+        double td = 1.0 + cd * xd;
+        if (!(td > 0.0)) continue;
+        double vd = td * td * td;
+        accept = log((double)U3) < 0.5 * xd * xd + dd - dd * vd + dd * log(vd);
+      }
+      if (accept) {
+        *ehat = (double)(d * v * kTf);
+        return 0;
+      }
+    }
+    return -4;
+  }
+  double kk = 1.5 * (double)(nc - 1);
+  double d = kk - 1.0 / 3.0;
+  double c = 1.0 / sqrt(9.0 * d);
+  for (uint32_t j = 0; j < 64; ++j) {
+    uint32_t wa[4], wb[4];
+    draw4(seed, ORACLE_PURPOSE_THERMO, cell, 1u + 2u * j, t, wa);
+    draw4(seed, ORACLE_PURPOSE_THERMO, cell, 2u + 2u * j, t, wb);
+    double U1 = u01_53(wa[0], wa[1]), U2 = u01_53(wa[2], wa[3]), U3 = u01_53(wb[0], wb[1]);
+    double x = sqrt(-2.0 * log(1.0 - U1)) * cos(TWO_PI * U2);
+    double t1 = 1.0 + c * x;
+    if (!(t1 > 0.0)) continue;
+    double v = t1 * t1 * t1;
+    if (log(U3) < 0.5 * x * x + d - d * v + d * log(v)) {
+      *ehat = d * v * kT;
+      return 0;
+    }
+  }
+  return -4;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry helpers                                                          */
+/* ------------------------------------------------------------------------ */
+int64_t oracle_num_cells(const oracle_params* p) {
+  int64_t nz = p->n[2] + (p->walls_z ? 2 : 0);
+  return (int64_t)p->n[0] * (int64_t)p->n[1] * nz;
+}
+
+/* Periodic wrap into [0, L). */
+static double wrap_d(double x, double L) {
+  if (x >= L) x -= L;
+  else if (x < 0.0) x += L;
+  if (!(x >= 0.0 && x < L)) {
+    x = x - L * floor(x / L);
+    if (!(x >= 0.0 && x < L)) x = 0.0;
+  }
+  return x;
+}
+static float wrap_f(float x, float L) {
+  if (x >= L) x -= L;
+  else if (x < 0.0f) x += L;
+  if (!(x >= 0.0f && x < L)) {
+    x = x - L * floorf(x / L);
+    if (!(x >= 0.0f && x < L)) x = 0.0f;
+  }
+  return x;
+}
+
+/* Sec. 3.4: cell of a position under grid shift s.  floor(x - s) is exact
+ * here (s is a multiple of 2^-32, |s| < 1/2), then periodic wrap of the cell
+ * coordinate; with walls the z layer index is floor(z - s_z) + 1 in
+ * [0, n_z + 1].  Cells are numbered x fastest. */
+static int32_t cell_of(const oracle_params* p, const double s[3], double x, double y, double z) {
+  int64_t c[3];
+  double r[3] = {x, y, z};
+  for (int k = 0; k < 3; ++k) {
+    int64_t i = (int64_t)floor(r[k] - s[k]);
+    if (k == 2 && p->walls_z) {
+      i += 1;
+      if (i < 0) i = 0;
+      if (i > p->n[2] + 1) i = p->n[2] + 1;
+    } else {
+      int64_t n = p->n[k];
+      i = ((i % n) + n) % n;
+    }
+    c[k] = i;
+  }
+  return (int32_t)(c[0] + (int64_t)p->n[0] * (c[1] + (int64_t)p->n[1] * c[2]));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2 Eq. (stream): ballistic streaming over dt.  With a body force g   */
+/* the motion is the constant-acceleration parabola.  With walls at z = 0    */
+/* and z = H the particle is moved to the wall at the hit time, its whole    */
+/* velocity reversed (no-slip bounce-back), and the remaining time streamed. */
+/* ------------------------------------------------------------------------ */
+static void stream_d(const oracle_params* p, double* r, double* v) {
+  const double dt = p->dt;
+  double L[3] = {(double)p->n[0], (double)p->n[1], (double)p->n[2]};
+  if (p->walls_z) {
+    double H = L[2];
+    double zn = fma(v[2], dt, r[2]);
+    if (!(zn >= 0.0 && zn < H)) {
+      double wall = (zn < 0.0) ? 0.0 : H;
+      double tau = (wall - r[2]) / v[2];
+      if (!(tau >= 0.0)) tau = 0.0;
+      if (tau > dt) tau = dt;
+      for (int k = 0; k < 2; ++k) {
+        r[k] = fma(v[k], tau, r[k]) + ((0.5 * p->g[k]) * tau) * tau;
+        v[k] = v[k] + p->g[k] * tau;
+      }
+      for (int k = 0; k < 3; ++k) v[k] = -v[k];
+      double rem = dt - tau;
+      for (int k = 0; k < 2; ++k) {
+        r[k] = fma(v[k], rem, r[k]) + ((0.5 * p->g[k]) * rem) * rem;
+        v[k] = v[k] + p->g[k] * rem;
+      }
+      double z = fma(v[2], rem, wall);
+      if (z < 0.0) z = 0.0;
+      if (z >= H) z = nextafter(H, 0.0);
+      r[2] = z;
+      for (int k = 0; k < 2; ++k) r[k] = wrap_d(r[k], L[k]);
+      return;
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    double hg = ((0.5 * p->g[k]) * dt) * dt;
+    r[k] = fma(v[k], dt, r[k]) + hg;
+    v[k] = v[k] + p->g[k] * dt;
+    if (!(k == 2 && p->walls_z)) r[k] = wrap_d(r[k], L[k]);
+  }
+}
+
+/* The same streaming rule with every operation rounded to float. */
+static void stream_f(const oracle_params* p, float* r, float* v) {
+  const float dt = (float)p->dt;
+  float L[3] = {(float)p->n[0], (float)p->n[1], (float)p->n[2]};
+  float g[3] = {(float)p->g[0], (float)p->g[1], (float)p->g[2]};
+  if (p->walls_z) {
+    float H = L[2];
+    float zn = fmaf(v[2], dt, r[2]);
+    if (!(zn >= 0.0f && zn < H)) {
+      float wall = (zn < 0.0f) ? 0.0f : H;
+      float tau = (wall - r[2]) / v[2];
+      if (!(tau >= 0.0f)) tau = 0.0f;
+      if (tau > dt) tau = dt;
+      for (int k = 0; k < 2; ++k) {
+        r[k] = fmaf(v[k], tau, r[k]) + ((0.5f * g[k]) * tau) * tau;
+        v[k] = v[k] + g[k] * tau;
+      }
+      for (int k = 0; k < 3; ++k) v[k] = -v[k];
+      float rem = dt - tau;
+      for (int k = 0; k < 2; ++k) {
+        r[k] = fmaf(v[k], rem, r[k]) + ((0.5f * g[k]) * rem) * rem;
+        v[k] = v[k] + g[k] * rem;
+      }
+      float z = fmaf(v[2], rem, wall);
+      if (z < 0.0f) z = 0.0f;
+      if (z >= H) z = nextafterf(H, 0.0f);
+      r[2] = z;
+      for (int k = 0; k < 2; ++k) r[k] = wrap_f(r[k], L[k]);
+      return;
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    float hg = (float)(((0.5 * p->g[k]) * p->dt) * p->dt);
+    float gdt = (float)(p->g[k] * p->dt);
+    r[k] = fmaf(v[k], dt, r[k]) + hg;
+    v[k] = v[k] + gdt;
+    if (!(k == 2 && p->walls_z)) r[k] = wrap_f(r[k], L[k]);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2 (solute) / Sec. 3.6: beads between collisions follow velocity      */
+/* Verlet with harmonic bonds U = k/2 (r - r0)^2 along each linear chain.    */
+/* ------------------------------------------------------------------------ */
+static void bond_forces(const oracle_params* p, int64_t nb, const double* r, double* F) {
+  double L[3] = {(double)p->n[0], (double)p->n[1], (double)p->n[2]};
+  int64_t cl = p->chain_len;
+  for (int64_t i = 0; i < nb; ++i) {
+    double f3[3] = {0.0, 0.0, 0.0};
+    int64_t b = i % cl;
+    for (int side = 0; side < 2; ++side) {
+      int64_t j;
+      if (side == 0) { if (b == 0) continue; j = i - 1; }
+      else { if (b == cl - 1) continue; j = i + 1; }
+      double d[3];
+      for (int k = 0; k < 3; ++k) {
+        d[k] = r[3 * j + k] - r[3 * i + k];
+        d[k] = d[k] - L[k] * nearbyint(d[k] / L[k]); /* minimum image */
+      }
+      double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (!(dist > 0.0)) continue;
+      double f = (p->bond_k * (dist - p->bond_r0)) / dist;
+      for (int k = 0; k < 3; ++k) f3[k] += f * d[k];
+    }
+    for (int k = 0; k < 3; ++k) F[3 * i + k] = f3[k];
+  }
+}
+
+static void md_substeps(const oracle_params* p, int64_t nb, double* r, double* v) {
+  double L[3] = {(double)p->n[0], (double)p->n[1], (double)p->n[2]};
+  double h = p->dt / (double)p->md_substeps;
+  double hh = (0.5 * h) / p->solute_mass;
+  double* F = (double*)malloc(sizeof(double) * 3 * (size_t)nb);
+  bond_forces(p, nb, r, F);
+  for (int s = 0; s < p->md_substeps; ++s) {
+    for (int64_t i = 0; i < 3 * nb; ++i) v[i] = v[i] + hh * F[i];
+    for (int64_t i = 0; i < nb; ++i)
+      for (int k = 0; k < 3; ++k) r[3 * i + k] = wrap_d(r[3 * i + k] + h * v[3 * i + k], L[k]);
+    bond_forces(p, nb, r, F);
+    for (int64_t i = 0; i < 3 * nb; ++i) v[i] = v[i] + hh * F[i];
+  }
+  free(F);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Walls: virtual particles fill the part of a wall-cut cell that lies       */
+/* outside the channel (Lamura et al. 2001): count with mean rho_v * f_out,  */
+/* Gaussian velocities of variance kT/m and zero mean.                       */
+/* ------------------------------------------------------------------------ */
+static double outside_fraction(const oracle_params* p, const double s[3], int64_t cz) {
+  double H = (double)p->n[2];
+  double lo = (double)(cz - 1) + s[2];
+  double hi = lo + 1.0;
+  double a = lo > 0.0 ? lo : 0.0;
+  double b = hi < H ? hi : H;
+  double inside = b - a;
+  if (inside < 0.0) inside = 0.0;
+  if (inside > 1.0) inside = 1.0;
+  return 1.0 - inside;
+}
+
+static int32_t virtual_count(const oracle_params* p, uint64_t t, uint32_t cell, double fout) {
+  if (!(fout > 0.0) || !(fout < 1.0)) return 0;
+  double lam = p->virt_density * fout;
+  double fl = floor(lam);
+  int32_t nv = (int32_t)fl;
+  uint32_t w[4];
+  draw4(p->seed, ORACLE_PURPOSE_VIRT, cell, 0u, t, w);
+  if (u01_53(w[0], w[1]) < lam - fl) nv += 1;
+  return nv;
+}
+
+static void virtual_velocity(const oracle_params* p, uint64_t t, uint32_t cell, int32_t q,
+                             double vv[3]) {
+  double sigma = sqrt(p->kT / p->mass);
+  for (int k = 0; k < 3; ++k) {
+    uint32_t w[4];
+    draw4(p->seed, ORACLE_PURPOSE_VIRT, cell, 1u + 3u * (uint32_t)q + (uint32_t)k, t, w);
+    double U = u01_53(w[0], w[1]), U2 = u01_53(w[2], w[3]);
+    vv[k] = sigma * (sqrt(-2.0 * log(1.0 - U)) * cos(TWO_PI * U2));
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2 Eq. (srd) written as a Rodrigues rotation of dv about the unit     */
+/* axis n by angle alpha:  dv' = dv cos a + (n x dv) sin a + n (n.dv)(1-cos a)*/
+/* ------------------------------------------------------------------------ */
+static void rotate_d(const double n[3], double ca, double sa, double omc, const double d[3],
+                     double out[3]) {
+  double nd = fma(n[2], d[2], fma(n[1], d[1], n[0] * d[0]));
+  double cr[3] = {fma(n[1], d[2], -(n[2] * d[1])), fma(n[2], d[0], -(n[0] * d[2])),
+                  fma(n[0], d[1], -(n[1] * d[0]))};
+  double ndo = nd * omc;
+  for (int k = 0; k < 3; ++k) out[k] = fma(n[k], ndo, fma(cr[k], sa, d[k] * ca));
+}
+static void rotate_f(const float n[3], float ca, float sa, float omc, const float d[3],
+                     float out[3]) {
+  float nd = fmaf(n[2], d[2], fmaf(n[1], d[1], n[0] * d[0]));
+  float cr[3] = {fmaf(n[1], d[2], -(n[2] * d[1])), fmaf(n[2], d[0], -(n[0] * d[2])),
+                 fmaf(n[0], d[1], -(n[1] * d[0]))};
+  float ndo = nd * omc;
+  for (int k = 0; k < 3; ++k) out[k] = fmaf(n[k], ndo, fmaf(cr[k], sa, d[k] * ca));
+}
+
+/* ------------------------------------------------------------------------ */
+/* One SRD step (Sec. 3 step flow)                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t* cnt;   /* real members (solvent + beads) */
+  int32_t* nsol;  /* solvent members                */
+  int32_t* nbead; /* bead members                   */
+  int32_t* nvirt; /* virtual particles (walls)      */
+  double* M;      /* FP64 mode: mass                */
+  double* P;      /* FP64 mode: momentum (3 per cell) */
+  double* E;      /* FP64 mode: kinetic energy about u */
+  int64_t* Qs;    /* MIXED: solvent sum of rne(v 2^32) (3 per cell) */
+  int64_t* Qx;    /* MIXED: beads/virtual sum of rne(m v 2^32) (3 per cell) */
+  int64_t* Es;    /* MIXED: solvent sum of rne(|v-u|^2 2^32) */
+  int64_t* Ex;    /* MIXED: beads/virtual sum of rne(m |v-u|^2 2^32) */
+  double* u;      /* centre-of-mass velocity (3 per cell) */
+  double* axis;   /* rotation axis (3 per cell) */
+  double* xi;     /* thermostat scale factor */
+} cellbuf;
+
+static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* vel, int64_t nb,
+                        double* spos, double* svel, uint64_t t, int32_t* cellid, cellbuf* cb,
+                        int64_t ncells) {
+  const int mixed = (p->precision == ORACLE_MIXED);
+  const double m = p->mass, Mb = p->solute_mass;
+  const double ca = cos(p->alpha), sa = sin(p->alpha), omc = 1.0 - ca;
+  int32_t status = 0;
+
+  /* Solute: MD substeps between collisions (Sec. 3.6, last paragraph). */
+  if (nb > 0) md_substeps(p, nb, spos, svel);
+
+  /* Grid shift for this step. */
+  double s[3];
+  oracle_shift(p->seed, t, s);
+
+  /* Stream the solvent. */
+  for (int64_t i = 0; i < n; ++i) {
+    if (mixed) {
+      float r[3] = {(float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2]};
+      float v[3] = {(float)vel[3 * i], (float)vel[3 * i + 1], (float)vel[3 * i + 2]};
+      stream_f(p, r, v);
+      for (int k = 0; k < 3; ++k) { pos[3 * i + k] = r[k]; vel[3 * i + k] = v[k]; }
+    } else {
+      stream_d(p, &pos[3 * i], &vel[3 * i]);
+    }
+  }
+
+  /* Bin solvent then beads. */
+  for (int64_t i = 0; i < n; ++i)
+    cellid[i] = cell_of(p, s, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]);
+  for (int64_t b = 0; b < nb; ++b)
+    cellid[n + b] = cell_of(p, s, spos[3 * b], spos[3 * b + 1], spos[3 * b + 2]);
+
+  /* Cell properties (Sec. 3.5): count, mass, momentum. */
+  memset(cb->cnt, 0, sizeof(int32_t) * ncells);
+  memset(cb->nsol, 0, sizeof(int32_t) * ncells);
+  memset(cb->nbead, 0, sizeof(int32_t) * ncells);
+  memset(cb->nvirt, 0, sizeof(int32_t) * ncells);
+  if (mixed) {
+    memset(cb->Qs, 0, sizeof(int64_t) * 3 * ncells);
+    memset(cb->Qx, 0, sizeof(int64_t) * 3 * ncells);
+    memset(cb->Es, 0, sizeof(int64_t) * ncells);
+    memset(cb->Ex, 0, sizeof(int64_t) * ncells);
+  } else {
+    memset(cb->M, 0, sizeof(double) * ncells);
+    memset(cb->P, 0, sizeof(double) * 3 * ncells);
+    memset(cb->E, 0, sizeof(double) * ncells);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t c = cellid[i];
+    cb->cnt[c] += 1;
+    cb->nsol[c] += 1;
+    for (int k = 0; k < 3; ++k) {
+      if (mixed) cb->Qs[3 * c + k] += llrint(vel[3 * i + k] * 0x1p32);
+      else cb->P[3 * c + k] += m * vel[3 * i + k];
+    }
+    if (!mixed) cb->M[c] += m;
+  }
+  for (int64_t b = 0; b < nb; ++b) {
+    int32_t c = cellid[n + b];
+    cb->cnt[c] += 1;
+    cb->nbead[c] += 1;
+    for (int k = 0; k < 3; ++k) {
+      if (mixed) cb->Qx[3 * c + k] += llrint((Mb * svel[3 * b + k]) * 0x1p32);
+      else cb->P[3 * c + k] += Mb * svel[3 * b + k];
+    }
+    if (!mixed) cb->M[c] += Mb;
+  }
+  /* Walls: virtual particles in occupied cells cut by a wall. */
+  if (p->walls_z) {
+    int64_t nxy = (int64_t)p->n[0] * p->n[1];
+    for (int64_t c = 0; c < ncells; ++c) {
+      if (cb->cnt[c] == 0) continue;
+      double fout = outside_fraction(p, s, c / nxy);
+      int32_t nv = virtual_count(p, t, (uint32_t)c, fout);
+      cb->nvirt[c] = nv;
+      for (int32_t q = 0; q < nv; ++q) {
+        double vv[3];
+        virtual_velocity(p, t, (uint32_t)c, q, vv);
+        for (int k = 0; k < 3; ++k) {
+          if (mixed) cb->Qx[3 * c + k] += llrint((m * vv[k]) * 0x1p32);
+          else cb->P[3 * c + k] += m * vv[k];
+        }
+        if (!mixed) cb->M[c] += m;
+      }
+    }
+  }
+
+  /* Centre-of-mass velocity u = P / M. */
+  const float mf = (float)m, Mbf = (float)Mb;
+  for (int64_t c = 0; c < ncells; ++c) {
+    if (cb->cnt[c] == 0) continue;
+    if (mixed) {
+      float Mx = (float)cb->nbead[c] * Mbf + (float)cb->nvirt[c] * mf;
+      float Mt = mf * (float)cb->nsol[c] + Mx;
+      for (int k = 0; k < 3; ++k) {
+        float P = mf * (float)cb->Qs[3 * c + k] + (float)cb->Qx[3 * c + k];
+        cb->u[3 * c + k] = (double)((P * 0x1p-32f) / Mt);
+      }
+    } else {
+      for (int k = 0; k < 3; ++k) cb->u[3 * c + k] = cb->P[3 * c + k] / cb->M[c];
+    }
+  }
+
+  /* Thermostat: kinetic energy about u, Eq. (thermo). */
+  if (p->thermostat) {
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t c = cellid[i];
+      if (mixed) {
+        float d[3];
+        for (int k = 0; k < 3; ++k) d[k] = (float)vel[3 * i + k] - (float)cb->u[3 * c + k];
+        float e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        cb->Es[c] += llrint((double)e * 0x1p32);
+      } else {
+        double d[3];
+        for (int k = 0; k < 3; ++k) d[k] = vel[3 * i + k] - cb->u[3 * c + k];
+        double e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        cb->E[c] += (0.5 * m) * e;
+      }
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+      int32_t c = cellid[n + b];
+      double d[3];
+      for (int k = 0; k < 3; ++k) d[k] = svel[3 * b + k] - cb->u[3 * c + k];
+      double e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (mixed) cb->Ex[c] += llrint((Mb * e) * 0x1p32);
+      else cb->E[c] += (0.5 * Mb) * e;
+    }
+    if (p->walls_z) {
+      for (int64_t c = 0; c < ncells; ++c) {
+        for (int32_t q = 0; q < cb->nvirt[c]; ++q) {
+          double vv[3], d[3];
+          virtual_velocity(p, t, (uint32_t)c, q, vv);
+          for (int k = 0; k < 3; ++k) d[k] = vv[k] - cb->u[3 * c + k];
+          double e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+          if (mixed) cb->Ex[c] += llrint((m * e) * 0x1p32);
+          else cb->E[c] += (0.5 * m) * e;
+        }
+      }
+    }
+  }
+
+  /* Per-cell axis and scale factor xi (Sec. 3.6). */
+  for (int64_t c = 0; c < ncells; ++c) {
+    cb->xi[c] = 1.0;
+    if (cb->cnt[c] == 0) continue;
+    oracle_axis(p->seed, t, (uint32_t)c, p->precision, &cb->axis[3 * c]);
+    int32_t nc = cb->cnt[c] + cb->nvirt[c];
+    if (p->thermostat && nc >= 2) {
+      double Ek;
+      if (mixed) {
+        float Ef = mf * (float)cb->Es[c] + (float)cb->Ex[c];
+        Ek = (double)((0.5f * Ef) * 0x1p-32f);
+      } else {
+        Ek = cb->E[c];
+      }
+      if (Ek > 0.0) {
+        double ehat;
+        int32_t st = oracle_gamma_draw(p->seed, t, (uint32_t)c, nc, p->kT, p->precision, &ehat);
+        if (st != 0) { status = st; continue; }
+        if (mixed) cb->xi[c] = (double)sqrtf((float)ehat / (float)Ek);
+        else cb->xi[c] = sqrt(ehat / Ek);
+      }
+    }
+  }
+
+  /* Collide, Eq. (srd) / Algorithm (SRD collision rule). */
+  const float caf = (float)ca, saf = (float)sa, omcf = (float)omc;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t c = cellid[i];
+    if (mixed) {
+      float nf[3], uf[3], d[3], rr[3];
+      for (int k = 0; k < 3; ++k) {
+        nf[k] = (float)cb->axis[3 * c + k];
+        uf[k] = (float)cb->u[3 * c + k];
+        d[k] = (float)vel[3 * i + k] - uf[k];
+      }
+      rotate_f(nf, caf, saf, omcf, d, rr);
+      float xif = (float)cb->xi[c];
+      for (int k = 0; k < 3; ++k) {
+        float r = p->thermostat ? xif * rr[k] : rr[k];
+        vel[3 * i + k] = (double)(uf[k] + r);
+      }
+    } else {
+      double d[3], rr[3];
+      for (int k = 0; k < 3; ++k) d[k] = vel[3 * i + k] - cb->u[3 * c + k];
+      rotate_d(&cb->axis[3 * c], ca, sa, omc, d, rr);
+      for (int k = 0; k < 3; ++k) {
+        double r = p->thermostat ? cb->xi[c] * rr[k] : rr[k];
+        vel[3 * i + k] = cb->u[3 * c + k] + r;
+      }
+    }
+  }
+  for (int64_t b = 0; b < nb; ++b) {
+    int32_t c = cellid[n + b];
+    double d[3], rr[3];
+    for (int k = 0; k < 3; ++k) d[k] = svel[3 * b + k] - cb->u[3 * c + k];
+    rotate_d(&cb->axis[3 * c], ca, sa, omc, d, rr);
+    for (int k = 0; k < 3; ++k) {
+      double r = p->thermostat ? cb->xi[c] * rr[k] : rr[k];
+      svel[3 * b + k] = cb->u[3 * c + k] + r;
+    }
+  }
+  return status;
+}
+
+static int32_t check_params(const oracle_params* p, int64_t n, int64_t nb) {
+  for (int k = 0; k < 3; ++k)
+    if (p->n[k] < 1) return -1;
+  if (n < 0 || nb < 0) return -1;
+  if (!(p->dt > 0.0) || !(p->mass > 0.0) || !(p->kT >= 0.0)) return -1;
+  if (p->walls_z && (p->g[2] != 0.0 || nb > 0)) return -1;
+  if (nb > 0 && (p->chain_len < 1 || nb % p->chain_len != 0 || p->md_substeps < 1 ||
+                 !(p->solute_mass > 0.0)))
+    return -1;
+  if (oracle_num_cells(p) > 2147483647LL) return -1;
+  return 0;
+}
+
+int32_t oracle_step(const oracle_params* p, int64_t n, double* pos, double* vel, int64_t nb,
+                    double* spos, double* svel, uint64_t* step, int64_t nsteps,
+                    int32_t* cell_out, int32_t* count_out) {
+  int32_t st = check_params(p, n, nb);
+  if (st) return st;
+  int64_t ncells = oracle_num_cells(p);
+  cellbuf cb;
+  cb.cnt = (int32_t*)calloc((size_t)ncells, sizeof(int32_t));
+  cb.nsol = (int32_t*)calloc((size_t)ncells, sizeof(int32_t));
+  cb.nbead = (int32_t*)calloc((size_t)ncells, sizeof(int32_t));
+  cb.nvirt = (int32_t*)calloc((size_t)ncells, sizeof(int32_t));
+  cb.M = (double*)calloc((size_t)ncells, sizeof(double));
+  cb.P = (double*)calloc((size_t)ncells * 3, sizeof(double));
+  cb.E = (double*)calloc((size_t)ncells, sizeof(double));
+  cb.Qs = (int64_t*)calloc((size_t)ncells * 3, sizeof(int64_t));
+  cb.Qx = (int64_t*)calloc((size_t)ncells * 3, sizeof(int64_t));
+  cb.Es = (int64_t*)calloc((size_t)ncells, sizeof(int64_t));
+  cb.Ex = (int64_t*)calloc((size_t)ncells, sizeof(int64_t));
+  cb.u = (double*)calloc((size_t)ncells * 3, sizeof(double));
+  cb.axis = (double*)calloc((size_t)ncells * 3, sizeof(double));
+  cb.xi = (double*)calloc((size_t)ncells, sizeof(double));
+  int32_t* cellid = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + nb + 1));
+  for (int64_t it = 0; it < nsteps && st == 0; ++it) {
+    st = one_step(p, n, pos, vel, nb, spos, svel, *step, cellid, &cb, ncells);
+    *step += 1;
+  }
+  if (nsteps > 0 && cell_out) memcpy(cell_out, cellid, sizeof(int32_t) * (size_t)(n + nb));
+  if (nsteps > 0 && count_out) memcpy(count_out, cb.cnt, sizeof(int32_t) * (size_t)ncells);
+  free(cellid);
+  free(cb.cnt); free(cb.nsol); free(cb.nbead); free(cb.nvirt);
+  free(cb.M); free(cb.P); free(cb.E);
+  free(cb.Qs); free(cb.Qx); free(cb.Es); free(cb.Ex);
+  free(cb.u); free(cb.axis); free(cb.xi);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.5 (last paragraph): net momentum, energy and temperature.          */
+/* ------------------------------------------------------------------------ */
+int32_t oracle_observables(const oracle_params* p, int64_t n, const double* pos,
+                           const double* vel, int64_t nb, const double* spos, const double* svel,
+                           double* out) {
+  int32_t st = check_params(p, n, nb);
+  if (st) return st;
+  const double m = p->mass, Mb = p->solute_mass;
+  double P[3] = {0, 0, 0}, KE = 0.0, Mtot = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double* v = &vel[3 * i];
+    for (int k = 0; k < 3; ++k) P[k] += m * v[k];
+    KE += (0.5 * m) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    Mtot += m;
+  }
+  for (int64_t b = 0; b < nb; ++b) {
+    const double* v = &svel[3 * b];
+    for (int k = 0; k < 3; ++k) P[k] += Mb * v[k];
+    KE += (0.5 * Mb) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    Mtot += Mb;
+  }
+  int64_t ntot = n + nb;
+  double Tkin = 0.0;
+  if (ntot > 1 && Mtot > 0.0) {
+    double pp = P[0] * P[0] + P[1] * P[1] + P[2] * P[2];
+    Tkin = 2.0 * (KE - pp / (2.0 * Mtot)) / (3.0 * (double)(ntot - 1));
+  }
+  /* Mean cell temperature on the unshifted grid. */
+  oracle_params q = *p;
+  q.walls_z = 0; /* unshifted cells of the channel: no extra layers needed */
+  int64_t nc = (int64_t)p->n[0] * p->n[1] * p->n[2];
+  int32_t* cnt = (int32_t*)calloc((size_t)nc, sizeof(int32_t));
+  double* M = (double*)calloc((size_t)nc, sizeof(double));
+  double* Pc = (double*)calloc((size_t)nc * 3, sizeof(double));
+  double* K = (double*)calloc((size_t)nc, sizeof(double));
+  double s0[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = 0; i < ntot; ++i) {
+    const double* r = i < n ? &pos[3 * i] : &spos[3 * (i - n)];
+    const double* v = i < n ? &vel[3 * i] : &svel[3 * (i - n)];
+    double mi = i < n ? m : Mb;
+    int32_t c = cell_of(&q, s0, r[0], r[1], r[2]);
+    cnt[c] += 1;
+    M[c] += mi;
+    for (int k = 0; k < 3; ++k) Pc[3 * c + k] += mi * v[k];
+    K[c] += (0.5 * mi) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  }
+  double Tsum = 0.0;
+  int64_t nT = 0, occ = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    if (cnt[c] >= 1) occ += 1;
+    if (cnt[c] >= 2) {
+      double pp = Pc[3 * c] * Pc[3 * c] + Pc[3 * c + 1] * Pc[3 * c + 1] + Pc[3 * c + 2] * Pc[3 * c + 2];
+      double Ek = K[c] - pp / (2.0 * M[c]);
+      Tsum += 2.0 * Ek / (3.0 * (double)(cnt[c] - 1));
+      nT += 1;
+    }
+  }
+  free(cnt); free(M); free(Pc); free(K);
+  out[0] = P[0]; out[1] = P[1]; out[2] = P[2];
+  out[3] = KE;
+  out[4] = Tkin;
+  out[5] = nT > 0 ? Tsum / (double)nT : 0.0;
+  out[6] = (double)occ;
+  out[7] = Mtot;
+  return 0;
+}
+
+int32_t oracle_profile(const oracle_params* p, int64_t n, const double* pos, const double* vel,
+                       int32_t nbins, double* out) {
+  if (nbins < 1 || n < 0) return -1;
+  double H = (double)p->n[2];
+  double* sum = (double*)calloc((size_t)nbins, sizeof(double));
+  int64_t* cnt = (int64_t*)calloc((size_t)nbins, sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t b = (int64_t)floor(pos[3 * i + 2] / H * (double)nbins);
+    if (b < 0) b = 0;
+    if (b >= nbins) b = nbins - 1;
+    sum[b] += vel[3 * i];
+    cnt[b] += 1;
+  }
+  for (int32_t b = 0; b < nbins; ++b) out[b] = cnt[b] ? sum[b] / (double)cnt[b] : 0.0;
+  free(sum);
+  free(cnt);
+  return 0;
+}

@@ -1,0 +1,113 @@
+/*
+ * mpcd_oracle.h -- plain, slow CPU oracle for one SRD (stochastic rotation
+ * dynamics) step of multiparticle collision dynamics.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  The GPU product path never
+ * links, calls or includes anything from this directory, and this code
+ * includes nothing from the product.
+ *
+ * What it computes (Howard, Panagiotopoulos & Nikoubashman, arXiv:1801.10187):
+ *   Sec. 2, Eq. (stream) : ballistic streaming r <- r + v dt
+ *   Sec. 2 / Sec. 3.4    : random grid shift, cubic cells of edge a = 1
+ *   Sec. 3.5             : per-cell mass, momentum and kinetic energy
+ *   Sec. 2, Eq. (srd)    : v <- u + R(alpha) (v - u), random axis per cell
+ *   Sec. 2, Eq. (thermo) : Maxwell-Boltzmann cell thermostat, xi = sqrt(E^/Ek)
+ *   Sec. 3.6             : cylindrical-projection axis, Marsaglia-Tsang Gamma
+ *                          draw with a Box-Muller normal, xi = 1 if Nc < 2
+ *   Sec. 2 / Sec. 3.6    : solute beads (velocity Verlet, harmonic bonds)
+ *                          binned and collided with the solvent
+ *   Sec. 3.5 (last par.) : net momentum / energy / temperature observables
+ * Walls with bounce-back and a body force are not given in the paper (Sec. 5
+ * lists them as future extensions); the reading implemented here is the one
+ * the design notes state.
+ *
+ * Two arithmetic modes:
+ *   ORACLE_FP64  : every quantity in double; sums in particle-index order.
+ *   ORACLE_MIXED : positions/velocities rounded to float after every store,
+ *                  cell momentum/energy sums in int64 fixed point (scale 2^32),
+ *                  rotation and thermostat draw in float with the operation
+ *                  order fixed below; solute beads stay double.
+ * State arrays are always passed as double; in MIXED mode they hold floats.
+ */
+#ifndef MPCD_ORACLE_H
+#define MPCD_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORACLE_FP64 = 0, ORACLE_MIXED = 1 };
+
+/* Random-stream purposes, XORed into the high key word (see oracle_key). */
+#define ORACLE_PURPOSE_SHIFT  0x53484654u
+#define ORACLE_PURPOSE_ROT    0x524F5441u
+#define ORACLE_PURPOSE_THERMO 0x54484D4Fu
+#define ORACLE_PURPOSE_VIRT   0x56495254u
+
+typedef struct {
+  int32_t n[3];          /* cells per axis; cell edge a = 1, box L_k = n_k   */
+  double dt;             /* collision time Delta t                          */
+  double alpha;          /* rotation angle (radians)                        */
+  double kT;             /* thermal energy                                  */
+  double mass;           /* solvent particle mass m                         */
+  uint64_t seed;         /* user seed                                       */
+  int32_t thermostat;    /* 1 = Maxwell-Boltzmann cell thermostat           */
+  int32_t walls_z;       /* 1 = bounce-back walls at z = 0 and z = n_z      */
+  double g[3];           /* body-force acceleration (g[2] must be 0 w/ walls)*/
+  double virt_density;   /* virtual-particle density in wall-cut cells      */
+  int32_t precision;     /* ORACLE_FP64 or ORACLE_MIXED                     */
+  int32_t chain_len;     /* beads per chain (solute)                        */
+  int32_t md_substeps;   /* velocity-Verlet substeps per collision          */
+  int32_t pad_;
+  double solute_mass;    /* bead mass M                                     */
+  double bond_k;         /* harmonic bond constant                          */
+  double bond_r0;        /* harmonic bond rest length                       */
+} oracle_params;
+
+/* Philox4x32-10 (Salmon et al., SC11) on one counter block. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Grid shift of step t: s_k = S_k * 2^-32, S_k in [-2^31, 2^31). */
+void oracle_shift(uint64_t seed, uint64_t t, double s[3]);
+
+/* Rotation axis of a cell at step t (cylindrical projection, Sec. 3.6). */
+void oracle_axis(uint64_t seed, uint64_t t, uint32_t cell, int32_t precision, double n[3]);
+
+/* Maxwell-Boltzmann kinetic-energy draw for a cell with nc >= 2 members:
+ * Gamma(3(nc-1)/2, kT) by Marsaglia-Tsang.  Returns 0, or -4 if 64 attempts
+ * were all rejected. */
+int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc,
+                          double kT, int32_t precision, double* ehat);
+
+/* Advance nsteps SRD steps in place.  pos/vel: n*3 (x,y,z per particle);
+ * spos/svel: nb*3 bead state (nb a multiple of chain_len).  *step is the
+ * step counter t, incremented per step.  If cell_out != NULL it receives the
+ * cell id of every particle (solvent then beads) at the last step; if
+ * count_out != NULL it receives the member count (solvent + beads) of every
+ * cell at the last step (oracle_num_cells entries).
+ * Returns 0, -1 invalid argument, -4 Gamma sampler cap reached. */
+int32_t oracle_step(const oracle_params* p, int64_t n, double* pos, double* vel,
+                    int64_t nb, double* spos, double* svel, uint64_t* step,
+                    int64_t nsteps, int32_t* cell_out, int32_t* count_out);
+
+/* Number of cells of the collision grid (n_z + 2 layers when walls_z). */
+int64_t oracle_num_cells(const oracle_params* p);
+
+/* Observables of the current state.  out[0..2] total momentum, out[3] total
+ * kinetic energy, out[4] kinetic temperature, out[5] mean cell temperature on
+ * the unshifted grid over cells with >= 2 members, out[6] number of occupied
+ * cells of that grid, out[7] total mass. */
+int32_t oracle_observables(const oracle_params* p, int64_t n, const double* pos,
+                           const double* vel, int64_t nb, const double* spos,
+                           const double* svel, double* out);
+
+/* Mean solvent v_x in nbins equal slabs of z in [0, n_z). */
+int32_t oracle_profile(const oracle_params* p, int64_t n, const double* pos,
+                       const double* vel, int32_t nbins, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

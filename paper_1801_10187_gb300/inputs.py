@@ -1,0 +1,98 @@
+"""Seeded synthetic inputs for SRD runs: the only module both the GPU path and
+the CPU oracle's tests draw from.  It holds no arithmetic of the method itself.
+
+Recipe (arXiv:1801.10187, Sec. 4 benchmark set-up and Sec. 4.1):
+  * solvent positions i.i.d. uniform in the box [0, n_x) x [0, n_y) x [0, n_z)
+    (cell edge a = 1), exactly ``density`` particles per cell on average
+    (N = density * n_x n_y n_z);
+  * velocities i.i.d. Gaussian with variance kT/m per component, then the mean
+    is subtracted in double precision (Sec. 4.1: a constant correction per
+    particle removes the net momentum); for the mixed-precision model the
+    corrected values are rounded to float afterwards, which leaves the small
+    residual the paper reports;
+  * solute: linear chains grown as random walks of step r0 from a uniform
+    start, wrapped into the box, Gaussian velocities with variance kT/M minus
+    their own mean.
+Everything is drawn from ``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Solvent:
+    pos: np.ndarray  # (N, 3) float64 (float32-representable for mixed precision)
+    vel: np.ndarray  # (N, 3) float64
+
+
+def _below(L: float, dtype) -> float:
+    return float(np.nextafter(dtype(L), dtype(0)))
+
+
+def solvent(n_cells, density: float, kT: float = 1.0, mass: float = 1.0, seed: int = 1,
+            mixed: bool = False, n_particles: int | None = None) -> Solvent:
+    """Uniform positions and zero-momentum Maxwell-Boltzmann velocities."""
+    nx, ny, nz = (int(x) for x in n_cells)
+    N = int(round(density * nx * ny * nz)) if n_particles is None else int(n_particles)
+    rng = np.random.default_rng(seed)
+    L = np.array([nx, ny, nz], dtype=np.float64)
+    pos = rng.random((N, 3)) * L
+    vel = rng.standard_normal((N, 3)) * np.sqrt(kT / mass)
+    if N > 0:
+        vel -= vel.mean(axis=0)
+    if mixed:
+        pos = pos.astype(np.float32)
+        for k in range(3):
+            over = pos[:, k] >= np.float32(L[k])
+            pos[over, k] = _below(L[k], np.float32)
+        pos = pos.astype(np.float64)
+        vel = vel.astype(np.float32).astype(np.float64)
+    else:
+        for k in range(3):
+            over = pos[:, k] >= L[k]
+            pos[over, k] = _below(L[k], np.float64)
+    return Solvent(np.ascontiguousarray(pos), np.ascontiguousarray(vel))
+
+
+def chains(n_cells, n_chains: int, chain_len: int, r0: float, kT: float = 1.0,
+           bead_mass: float = 5.0, seed: int = 3):
+    """Random-walk chains (bond length r0) wrapped into the periodic box."""
+    rng = np.random.default_rng(seed)
+    L = np.array([int(x) for x in n_cells], dtype=np.float64)
+    nb = n_chains * chain_len
+    pos = np.zeros((nb, 3))
+    for c in range(n_chains):
+        start = rng.random(3) * L
+        steps = rng.standard_normal((chain_len - 1, 3))
+        steps /= np.linalg.norm(steps, axis=1, keepdims=True)
+        walk = np.vstack([start, start + np.cumsum(steps * r0, axis=0)])
+        pos[c * chain_len:(c + 1) * chain_len] = walk
+    pos = np.mod(pos, L)
+    for k in range(3):
+        over = pos[:, k] >= L[k]
+        pos[over, k] = _below(L[k], np.float64)
+    vel = rng.standard_normal((nb, 3)) * np.sqrt(kT / bead_mass)
+    if nb > 0:
+        vel -= vel.mean(axis=0)
+    return np.ascontiguousarray(pos), np.ascontiguousarray(vel)
+
+
+# Named workloads (sizes of the benchmark set-ups).  Each entry gives the
+# keyword arguments of the SRD parameters and of the solvent generator.
+WORKLOADS = {
+    "srd-10c-rho5-fp64": dict(n=(10, 10, 10), density=5, alpha_deg=130.0, dt=0.1, kT=1.0,
+                              seed=1, thermostat=False, precision="fp64", steps=1000),
+    "srd-100c-rho10-fp64": dict(n=(100, 100, 100), density=10, alpha_deg=130.0, dt=0.1,
+                                kT=1.0, seed=2, thermostat=False, precision="fp64", steps=2000),
+    "srd-100c-rho10-mixed": dict(n=(100, 100, 100), density=10, alpha_deg=130.0, dt=0.1,
+                                 kT=1.0, seed=2, thermostat=False, precision="mixed",
+                                 steps=2000),
+    "srd-250c-rho5-mixed-solute": dict(n=(250, 250, 250), density=5, alpha_deg=130.0, dt=0.1,
+                                       kT=1.0, seed=3, thermostat=True, precision="mixed",
+                                       steps=500, n_chains=2000, chain_len=50,
+                                       bead_mass=5.0, bond_k=1000.0, bond_r0=0.5,
+                                       md_substeps=10),
+}
