@@ -74,6 +74,9 @@ def _load():
         _lib.oracle_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32),
                                               P(ctypes.c_uint32)]
         _lib.oracle_shift.argtypes = [u64, u64, P(d)]
+        _lib.oracle_cos_sin_turn_f.argtypes = [ctypes.c_uint32, P(ctypes.c_float), P(ctypes.c_float)]
+        _lib.oracle_log_f.argtypes = [ctypes.c_float]
+        _lib.oracle_log_f.restype = ctypes.c_float
         _lib.oracle_axis.argtypes = [u64, u64, ctypes.c_uint32, i32, P(d)]
         _lib.oracle_gamma_draw.argtypes = [u64, u64, ctypes.c_uint32, i32, d, i32, P(d)]
         _lib.oracle_gamma_draw.restype = i32
@@ -141,6 +144,18 @@ def philox(ctr, key):
     o = (ctypes.c_uint32 * 4)()
     lib.oracle_philox4x32_10(c, k, o)
     return [int(x) for x in o]
+
+
+def cos_sin_turn_f(w: int):
+    """The mixed model's float (cos, sin) of 2 pi w / 2^32."""
+    c, s = ctypes.c_float(), ctypes.c_float()
+    _load().oracle_cos_sin_turn_f(int(w) & 0xFFFFFFFF, ctypes.byref(c), ctypes.byref(s))
+    return c.value, s.value
+
+
+def log_f(x: float) -> float:
+    """The mixed model's float natural logarithm."""
+    return _load().oracle_log_f(float(np.float32(x)))
 
 
 def shift(seed: int, t: int) -> np.ndarray:

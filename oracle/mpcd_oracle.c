@@ -61,19 +61,77 @@ static double u01_53(uint32_t hi, uint32_t lo) {
 
 static const double TWO_PI = 6.283185307179586;
 
-/* cos and sin of 2 pi w / 2^32 in float: the top two bits of w pick the
- * quadrant (an exact swap/negation), the other 30 bits give the angle in
- * [0, pi/2), so the float argument carries no large-angle rounding. */
-static void cos_sin_turn_f(uint32_t w, float* c, float* s) {
-  uint32_t q = w >> 30;
-  float f = (float)(w & 0x3FFFFFFFu) * 0x1p-30f;
-  float th = f * 1.57079637f;
-  float ct = cosf(th), st = sinf(th);
-  if (q == 0) { *c = ct; *s = st; }
-  else if (q == 1) { *c = -st; *s = ct; }
-  else if (q == 2) { *c = -ct; *s = -st; }
-  else { *c = st; *s = -ct; }
+/* ------------------------------------------------------------------------ */
+/* Float sin, cos and log used by the mixed model, built from IEEE basic     */
+/* operations only so that every platform rounds them identically:           */
+/*   sin, cos on [0, pi/4]: Taylor series through x^9 / x^10 (truncation      */
+/*   below 2e-9);  log: x = m 2^e with m in [sqrt(1/2), sqrt(2)), then        */
+/*   ln m = 2 atanh(t), t = (m-1)/(m+1), series through t^11 (below 1e-9).    */
+/* ------------------------------------------------------------------------ */
+static void sincos_series_f(float x, float* s, float* c) {
+  const float x2 = x * x;
+  const float s3 = (float)(-1.0 / 6.0), s5 = (float)(1.0 / 120.0);
+  const float s7 = (float)(-1.0 / 5040.0), s9 = (float)(1.0 / 362880.0);
+  const float c2 = -0.5f, c4 = (float)(1.0 / 24.0), c6 = (float)(-1.0 / 720.0);
+  const float c8 = (float)(1.0 / 40320.0), c10 = (float)(-1.0 / 3628800.0);
+  *s = x + x * (x2 * (s3 + x2 * (s5 + x2 * (s7 + x2 * s9))));
+  *c = 1.0f + x2 * (c2 + x2 * (c4 + x2 * (c6 + x2 * (c8 + x2 * c10))));
 }
+
+/* cos and sin of 2 pi w / 2^32: the top three bits of w give the octant, the
+ * other 29 the position inside it; odd octants are measured back from their
+ * upper end, so the series argument stays in [0, pi/4] and the octant map is
+ * an exact swap / negation. */
+static void cos_sin_turn_f(uint32_t w, float* c, float* s) {
+  const uint32_t o = w >> 29;
+  const uint32_t f = w & 0x1FFFFFFFu;
+  const uint32_t g = (o & 1u) ? (0x20000000u - f) : f;
+  const float quarter_pi = (float)(3.14159265358979323846 / 4.0);
+  const float x = ((float)g * 0x1p-29f) * quarter_pi;
+  float sb, cb;
+  sincos_series_f(x, &sb, &cb);
+  switch (o) {
+    case 0: *c = cb; *s = sb; break;
+    case 1: *c = sb; *s = cb; break;
+    case 2: *c = -sb; *s = cb; break;
+    case 3: *c = -cb; *s = sb; break;
+    case 4: *c = -cb; *s = -sb; break;
+    case 5: *c = -sb; *s = -cb; break;
+    case 6: *c = sb; *s = -cb; break;
+    default: *c = cb; *s = -sb; break;
+  }
+}
+
+static float log_series_f(float x) {
+  if (!(x > 0.0f)) return x == 0.0f ? -INFINITY : NAN;
+  if (isinf(x)) return x;
+  int e = 0;
+  uint32_t b;
+  memcpy(&b, &x, 4);
+  if ((b >> 23) == 0) { /* subnormal: scale into the normal range */
+    x = x * 0x1p23f;
+    memcpy(&b, &x, 4);
+    e = -23;
+  }
+  e += (int)((b >> 23) & 0xFFu) - 127;
+  uint32_t mb = (b & 0x7FFFFFu) | 0x3F800000u;
+  float m;
+  memcpy(&m, &mb, 4);
+  if (m > 1.41421354f) {
+    m = m * 0.5f;
+    e += 1;
+  }
+  const float t = (m - 1.0f) / (m + 1.0f);
+  const float t2 = t * t;
+  const float l3 = (float)(1.0 / 3.0), l5 = (float)(1.0 / 5.0), l7 = (float)(1.0 / 7.0);
+  const float l9 = (float)(1.0 / 9.0), l11 = (float)(1.0 / 11.0);
+  const float series = 1.0f + t2 * (l3 + t2 * (l5 + t2 * (l7 + t2 * (l9 + t2 * l11))));
+  const float ln2 = (float)0.69314718055994530942;
+  return (float)e * ln2 + (2.0f * t) * series;
+}
+
+void oracle_cos_sin_turn_f(uint32_t w, float* c, float* s) { cos_sin_turn_f(w, c, s); }
+float oracle_log_f(float x) { return log_series_f(x); }
 
 /* ------------------------------------------------------------------------ */
 /* Sec. 2 / Sec. 3.4: random grid shift, one vector per step.  Quantised to  */
@@ -145,12 +203,12 @@ int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, 
       float U3 = (float)wb[0] * 0x1p-32f;
       float c2, s2;
       cos_sin_turn_f(wa[2], &c2, &s2);
-      float x = sqrtf(-2.0f * logf(e1)) * c2;
+      float x = sqrtf(-2.0f * log_series_f(e1)) * c2;
       float t1 = 1.0f + c * x;
       if (!(t1 > 0.0f)) continue;
       float v = t1 * t1 * t1;
-      float lhs = logf(U3);
-      float rhs = 0.5f * (x * x) + d - d * v + d * logf(v);
+      float lhs = log_series_f(U3);
+      float rhs = 0.5f * (x * x) + d - d * v + d * log_series_f(v);
       float diff = lhs - rhs;
       int accept;
       if (fabsf(diff) > 1e-3f * (1.0f + d)) {

@@ -69,6 +69,11 @@ typedef struct {
 /* Philox4x32-10 (Salmon et al., SC11) on one counter block. */
 void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
+/* The mixed model's own float functions (exposed for their pins):
+ * cos and sin of 2 pi w / 2^32, and the natural logarithm. */
+void oracle_cos_sin_turn_f(uint32_t w, float* c, float* s);
+float oracle_log_f(float x);
+
 /* Grid shift of step t: s_k = S_k * 2^-32, S_k in [-2^31, 2^31). */
 void oracle_shift(uint64_t seed, uint64_t t, double s[3]);
 

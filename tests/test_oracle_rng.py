@@ -135,3 +135,40 @@ def test_thermostat_mixed_draw_tracks_fp64_draw():
         if abs(a - b) <= 1e-5 * max(1.0, a):
             close += 1
     assert close >= 295
+
+
+def _ulp32(x):
+    x = np.abs(np.asarray(x, dtype=np.float32))
+    return np.spacing(np.maximum(x, np.float32(2.0**-126))).astype(np.float64)
+
+
+def test_float_turn_cos_sin_within_two_ulp():
+    """The mixed model's own cos/sin of 2 pi w / 2^32 (octant reduction and
+    Taylor series) against numpy's double-precision cos/sin."""
+    rng = np.random.default_rng(1)
+    words = np.concatenate([rng.integers(0, 2**32, 20000, dtype=np.uint64),
+                            np.array([0, 1, 2**29 - 1, 2**29, 2**29 + 1, 2**30, 2**31,
+                                      3 * 2**30, 2**32 - 1], dtype=np.uint64)])
+    got = np.array([oracle.cos_sin_turn_f(int(w)) for w in words], dtype=np.float64)
+    ang = 2 * np.pi * words.astype(np.float64) / 2.0**32
+    ref = np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    err = np.abs(got - ref)
+    # absolute error in units of the float spacing near 1 (the values are <= 1)
+    assert err.max() < 2.0 * 2.0**-24
+    # exact quadrant points
+    assert oracle.cos_sin_turn_f(0) == (1.0, 0.0)
+    c, s = oracle.cos_sin_turn_f(2**30)
+    assert abs(c) < 1e-7 and s == 1.0
+
+
+def test_float_log_within_three_ulp():
+    rng = np.random.default_rng(2)
+    xs = np.concatenate([np.exp(rng.uniform(-85, 85, 20000)), rng.uniform(0.5, 2.0, 20000),
+                         [1.0, 2.0, 0.5, 2.0**-32, 1 - 2.0**-24, 1.41421354, 1.41421365]])
+    xs = xs.astype(np.float32)
+    got = np.array([oracle.log_f(x) for x in xs], dtype=np.float64)
+    ref = np.log(xs.astype(np.float64))
+    ulps = np.abs(got - ref) / _ulp32(ref)
+    assert ulps.max() <= 3.0
+    assert oracle.log_f(1.0) == 0.0
+    assert oracle.log_f(0.0) == -np.inf
