@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""SRD (MPCD) step throughput on GB300: particle-steps/s and HBM roofline.
+
+Default workload: the 100 x 100 x 100-cell SRD solvent at 10 particles per
+cell (10^7 particles), mixed precision (FP32 particles, int64 fixed-point cell
+sums), alpha = 130 deg, dt = 0.1, kT = 1, grid shift every step, reorder every
+25 steps, 2000 steps.  Synthetic, seeded inputs (uniform positions,
+zero-momentum Maxwell-Boltzmann velocities).
+
+One JSON line on rank 0:
+  value     particle-steps/s of the whole job, state resident in HBM, timed with
+            CUDA events on the stream the kernels run on
+  e2e       same metric through the C ABI with host arrays (set_state, K steps,
+            get_state), wall clock
+  roofline  dominant kernel: algorithmic bytes / its event-timed duration
+  cpu_baseline  the CPU oracle, single thread, on a bounded sample
+--impl reference times the CPU oracle (the reference of this build) instead.
+Multi-GPU (torchrun): independent replica boxes per rank (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1801_10187_gb300 import inputs  # noqa: E402
+
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "MPCD particle-steps/s"
+UNIT = "particle-steps/s"
+# kernels launched per step (stream_bin, 3 scan phases, scatter, permute, swap,
+# collide, end_step); the solute adds md_bin, 3 bead-scan phases, bead scatter
+LAUNCHES_PER_STEP = 9
+LAUNCHES_PER_STEP_SOLUTE = 14
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload_cfg(name):
+    if name not in inputs.WORKLOADS:
+        raise SystemExit(f"unknown workload {name}; choose from {sorted(inputs.WORKLOADS)}")
+    return dict(inputs.WORKLOADS[name])
+
+
+def box_kwargs(cfg):
+    kw = dict(n=cfg["n"], dt=cfg["dt"], alpha_deg=cfg["alpha_deg"], kT=cfg["kT"],
+              seed=cfg["seed"], thermostat=cfg["thermostat"], precision=cfg["precision"],
+              sort_period=cfg.get("sort_period", 0))
+    if cfg.get("n_chains"):
+        kw.update(chain_len=cfg["chain_len"], md_substeps=cfg["md_substeps"],
+                  solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"])
+    return kw
+
+
+def make_state(cfg, n=None, seed_offset=0):
+    n = n or cfg["n"]
+    s = inputs.solvent(n, cfg["density"], kT=cfg["kT"], seed=cfg["seed"] + seed_offset,
+                       mixed=cfg["precision"] == "mixed")
+    sp = sv = None
+    if cfg.get("n_chains"):
+        sp, sv = inputs.chains(n, cfg["n_chains"], cfg["chain_len"], cfg["bond_r0"],
+                               kT=cfg["kT"], bead_mass=cfg["bead_mass"],
+                               seed=cfg["seed"] + 1000 + seed_offset)
+    return s, sp, sv
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_rate(cfg, budget_s, steps=None, warmup=0):
+    """Time the CPU oracle (as it stands, one thread) on the workload.  The box
+    is the full workload box when it fits the budget, else a cube of the same
+    density, parameters and precision scaled down so that (warmup + steps)
+    oracle steps take about budget_s."""
+    import oracle
+    oracle.build()
+    full_cells = int(np.prod(cfg["n"]))
+    ns_per_ps = 170.0  # rough oracle cost per particle-step, for sizing only
+    nsteps = steps if steps else 3
+    want_ps = budget_s * 1e9 / ns_per_ps / max(1, nsteps + warmup)
+    cells = min(full_cells, max(27, int(want_ps / cfg["density"])))
+    if cells < full_cells:
+        edge = max(3, int(round(cells ** (1 / 3))))
+        n = (edge, edge, edge)
+    else:
+        n = tuple(cfg["n"])
+    s, sp, sv = make_state(cfg, n=n)
+    prec = oracle.MIXED if cfg["precision"] == "mixed" else oracle.FP64
+    okw = dict(n=n, dt=cfg["dt"], alpha_deg=cfg["alpha_deg"], kT=cfg["kT"], seed=cfg["seed"],
+               thermostat=cfg["thermostat"], precision=prec)
+    if cfg.get("n_chains"):
+        nch = max(1, int(round(cfg["n_chains"] * np.prod(n) / full_cells)))
+        sp, sv = inputs.chains(n, nch, cfg["chain_len"], cfg["bond_r0"], kT=cfg["kT"],
+                               bead_mass=cfg["bead_mass"], seed=cfg["seed"] + 1000)
+        okw.update(chain_len=cfg["chain_len"], md_substeps=cfg["md_substeps"],
+                   solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"])
+    p = oracle.Params(**okw)
+    st = oracle.State(s.pos, s.vel, sp if sp is not None else np.zeros((0, 3)),
+                      sv if sv is not None else np.zeros((0, 3)))
+    if warmup:
+        oracle.step(p, st, warmup)
+    t0 = time.perf_counter()
+    oracle.step(p, st, nsteps)
+    dt = time.perf_counter() - t0
+    npart = st.pos.shape[0] + st.spos.shape[0]
+    rate = npart * nsteps / dt
+    sample = (f"{nsteps} steps of a {n[0]}x{n[1]}x{n[2]}-cell box ({npart} particles), same "
+              f"density/parameters/precision as the workload")
+    return rate, sample, dt, nsteps
+
+
+# ------------------------------------------------------------------ traffic record
+def kernel_traffic(kernel, workload):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    ent = rec.get(f"{kernel}/{workload}")
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    if h != ent.get("source_sha256_16"):
+        return None
+    return ent["dram_bytes_per_launch"] * ent.get("scale_to_workload", 1.0)
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="srd-100c-rho10-mixed")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = workload_cfg(args.workload)
+    K = args.steps if args.steps is not None else cfg["steps"]
+    W = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    config = {"workload": args.workload, "cells": list(cfg["n"]), "density": cfg["density"],
+              "precision": cfg["precision"], "thermostat": cfg["thermostat"],
+              "alpha_deg": cfg["alpha_deg"], "dt": cfg["dt"], "kT": cfg["kT"],
+              "sort_period": cfg.get("sort_period", 0) or 25,
+              "particles_per_gpu": int(round(cfg["density"] * np.prod(cfg["n"]))),
+              "parallelism": f"replicas{world}" if world > 1 else "single"}
+    if cfg.get("n_chains"):
+        config["solute"] = {"chains": cfg["n_chains"], "beads_per_chain": cfg["chain_len"]}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        budget = 150.0
+        rate, sample, dt, nsteps = oracle_rate(cfg, budget, steps=K, warmup=W)
+        line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+                "n_gpus": args.gpus, "steps": K, "warmup": W,
+                "ms_per_step": 1e3 * dt / nsteps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if cfg["precision"] == "fp64"
+                else "f32+i64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    import paper_1801_10187_gb300 as pkg
+
+    s, sp, sv = make_state(cfg, seed_offset=rank)
+    N = s.pos.shape[0] + (sp.shape[0] if sp is not None else 0)
+    # a dedicated (non-default) stream: the library orders all its work on it
+    # and the CUDA events below are recorded on the same stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    assert stream.cuda_stream != 0
+    box = pkg.Box(stream=stream.cuda_stream, **box_kwargs(cfg))
+    box.set_state(s.pos, s.vel, sp, sv)
+    box.step(W)
+    torch.cuda.synchronize()
+
+    # ---- device-resident throughput ----
+    sampler = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    box.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * K * world / (ms * 1e-3)
+
+    # ---- per-phase times (event-timed eager steps, same stream) ----
+    phases = box.phase_times(min(K, 50))
+    hbm_peak, peak_src = load_peaks()
+    es = 4 if cfg["precision"] == "mixed" else 8
+    alg = {"stream_bin": (2 * 3 * es + 3 * es) * s.pos.shape[0],   # read r, v; write r
+           "collide": (2 * 3 * es) * s.pos.shape[0]}                # read v; write v
+    dom = max(("stream_bin", "collide"), key=lambda k: phases.get(k, 0.0))
+    dom_ms = phases[dom]
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
+    traffic = kernel_traffic(dom, args.workload)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                "peak_source": peak_src,
+                "alg_bytes_per_particle": alg[dom] / s.pos.shape[0]}
+    step_bytes = (2 * 3 * es + 3 * 3 * es)  # 2 s_r + 3 s_v per particle-step
+    step_gbs = step_bytes * N * K / (ms * 1e-3) / 1e9 / world
+    hbm_step = {"bytes_per_particle_step": step_bytes, "achieved_gbs": step_gbs,
+                "frac_of_peak": step_gbs / hbm_peak, "frac_of_8tbs": step_gbs / 8000.0,
+                "phase_ms": phases}
+
+    # ---- end to end through the C ABI with host arrays ----
+    e2e = None
+    if not args.no_e2e:
+        Ke = K
+        box2 = pkg.Box(stream=stream.cuda_stream, **box_kwargs(cfg))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        box2.set_state(s.pos, s.vel, sp, sv)
+        box2.step(Ke)
+        out = box2.get_state()
+        t1 = time.perf_counter()
+        wall = t1 - t0
+        if dist:
+            t = torch.tensor([wall], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        assert out[4] == Ke
+        h2d = s.pos.shape[0] * 2 * 3 * es + (0 if sp is None else sp.shape[0] * 48)
+        e2e = {"value": N * Ke * world / wall, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / Ke, "d2h_bytes_per_step": h2d / Ke,
+               "steps_per_job": Ke, "wall_s": wall}
+        box2.close()
+
+    # ---- CPU baseline (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sample, dt, nsteps = oracle_rate(cfg, 20.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    launches = (LAUNCHES_PER_STEP_SOLUTE if cfg.get("n_chains") else LAUNCHES_PER_STEP) * K
+    config["l2"] = (f"state {s.pos.shape[0] * 6 * es / 1e6:.0f} MB > 129 MB L2 (inputs larger "
+                    "than L2; no flush)")
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None,
+                "dtype": "f64" if cfg["precision"] == "fp64" else "f32+i64",
+                "data": "synthetic", "config": config, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": launches, "roofline": roofline, "hbm_step": hbm_step,
+                "cpu_baseline": cpu}
+        print(json.dumps(line))
+    box.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

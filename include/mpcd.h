@@ -1,0 +1,199 @@
+/*
+ * mpcd.h -- C ABI of libmpcd, a single-GPU (NVIDIA GB300, sm_103a)
+ * implementation of the per-step hot path of multiparticle collision dynamics
+ * with the stochastic rotation dynamics (SRD) collision rule.
+ *
+ * Method: Howard, Panagiotopoulos & Nikoubashman, "Efficient mesoscale
+ * hydrodynamics: multiparticle collision dynamics with massively parallel GPU
+ * acceleration", arXiv:1801.10187.  One step is (Sec. 3, step flow):
+ *   [solute velocity-Verlet substeps]           Sec. 2 / Sec. 3.6 (solute)
+ *   ballistic streaming r <- r + v dt           Sec. 2, Eq. (stream)
+ *   random grid shift, binning into cells       Sec. 2, Sec. 3.4
+ *   [periodic reorder of particles by cell]     Sec. 3.8
+ *   per-cell mass / momentum / kinetic energy   Sec. 3.5
+ *   per-cell random axis [+ MB thermostat]      Sec. 3.6, Eq. (thermo)
+ *   v <- u + xi R(alpha) (v - u)                Sec. 2, Eq. (srd); Sec. 3.6 algorithm
+ *
+ * Conventions
+ *   - Lengths are in units of the cell edge a: the cell edge is 1 and the box
+ *     is [0, n_x) x [0, n_y) x [0, n_z).  Positions outside are wrapped.
+ *   - Host arrays are caller owned, row major (x, y, z per particle), and are
+ *     only read or written during the call.  "_device" variants take device
+ *     pointers to memory on the context's device; the call orders itself on
+ *     the context's stream and does not synchronise unless stated.
+ *   - Particles keep their input order (their tag) in every output.
+ *   - Every call returns MPCD_OK (0) or a negative code below; the message of
+ *     the last failure on the calling thread is mpcd_last_error().
+ *   - Nothing here falls back to the CPU: without a usable CUDA device the
+ *     creating calls fail with MPCD_ECUDA.
+ */
+#ifndef MPCD_H
+#define MPCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPCD_OK 0
+#define MPCD_EINVAL (-1)   /* invalid argument                                */
+#define MPCD_ENOMEM (-2)   /* device memory exhausted                         */
+#define MPCD_ECUDA (-3)    /* CUDA runtime error (message in mpcd_last_error) */
+#define MPCD_EDEVICE (-4)  /* a device-side limit was hit (thermostat sampler  */
+                           /* gave up after 64 attempts, or a cell id left the */
+                           /* grid because a position was not finite)          */
+#define MPCD_ESTATE (-5)   /* no state has been set                           */
+
+typedef enum { MPCD_FP64 = 0, MPCD_MIXED = 1 } mpcd_precision;
+
+/* SRD parameters (Sec. 2; Sec. 4 benchmark values in brackets).  Plain
+ * values, copied at create time. */
+typedef struct {
+  int32_t n[3];          /* cells per axis                                   */
+  int32_t precision;     /* mpcd_precision: FP64, or MIXED = float particles, */
+                         /* int64 fixed-point cell sums (Sec. 4.1 model)     */
+  double a;              /* cell edge; must be 1.0                           */
+  double dt;             /* collision time Delta t [0.1]                      */
+  double alpha;          /* rotation angle in radians [130 degrees]          */
+  double kT;             /* thermal energy [1]                               */
+  double mass;           /* solvent particle mass m [1]                      */
+  uint64_t seed;         /* seed of all random draws                         */
+  int32_t thermostat;    /* 1: Maxwell-Boltzmann cell thermostat (Eq. thermo)*/
+  int32_t sort_period;   /* reorder particles every k steps (Sec. 3.8) [25]; */
+                         /* 0 = 25, negative = never                         */
+  int32_t walls_z;       /* 1: no-slip bounce-back walls at z = 0, z = n_z   */
+  int32_t reserved0;
+  double body_force[3];  /* constant acceleration g; g_z must be 0 w/ walls  */
+  double virt_density;   /* density of virtual wall particles; 0 = N / V     */
+  int32_t chain_len;     /* solute: beads per linear chain (0 = no solute)   */
+  int32_t md_substeps;   /* solute: velocity-Verlet substeps per collision   */
+  double solute_mass;    /* solute: bead mass M                              */
+  double bond_k;         /* solute: harmonic bond constant k                 */
+  double bond_r0;        /* solute: harmonic bond rest length r0             */
+} mpcd_params;
+
+/* Observables of the current state (Sec. 3.5, last paragraph). */
+typedef struct {
+  double P[3];           /* total momentum sum m v                           */
+  double KE;             /* total kinetic energy sum m v^2 / 2               */
+  double T_kin;          /* 2 (KE - |P|^2 / 2M) / (3 (N - 1))                */
+  double T_cell_mean;    /* mean over cells of the unshifted grid with >= 2   */
+                         /* members of 2 Ek / (3 (Nc - 1))                    */
+  double mass;           /* total mass                                        */
+  int64_t n;             /* particles (solvent + solute)                      */
+  int64_t occupied_cells;/* cells of the unshifted grid with >= 1 member      */
+  uint64_t step;         /* step counter                                      */
+} mpcd_obs;
+
+typedef struct mpcd_ctx mpcd_ctx;
+
+/* Create a context for one box on the current CUDA device.  stream: a
+ * cudaStream_t to order all work on (NULL = a stream the library creates).
+ * Allocates the cell arrays; particle arrays are sized by set_state.
+ * Errors: EINVAL (bad parameters, a != 1), ENOMEM, ECUDA. */
+int mpcd_create(const mpcd_params* params, void* stream, mpcd_ctx** out);
+
+/* Load the state (Sec. 3.2 particle data).  pos/vel: n_solvent x 3 doubles
+ * (in MIXED mode rounded to float); solute_pos/solute_vel: n_solute x 3
+ * doubles or NULL when n_solute == 0 (n_solute a multiple of chain_len).
+ * step: the step counter t that keys the random draws.  Synchronises.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int mpcd_set_state(mpcd_ctx* ctx, int64_t n_solvent, const double* pos, const double* vel,
+                   int64_t n_solute, const double* solute_pos, const double* solute_vel,
+                   uint64_t step);
+
+/* Same, from device memory: pos/vel are n_solvent x 3 arrays of float
+ * (MIXED) or double (FP64) on the context's device. */
+int mpcd_set_state_device(mpcd_ctx* ctx, int64_t n_solvent, const void* pos, const void* vel,
+                          uint64_t step);
+
+/* Advance nsteps SRD steps.  Enqueued on the context's stream (replays of a
+ * captured CUDA graph); returns without synchronising.  A device-side limit
+ * hit during these steps is reported by the next synchronising call.
+ * Errors: ESTATE, EINVAL (nsteps < 0), ECUDA. */
+int mpcd_step(mpcd_ctx* ctx, int64_t nsteps);
+
+/* Copy the state out in input (tag) order; arrays as for set_state (solute
+ * arrays may be NULL).  Synchronises.  Errors: ESTATE, ECUDA, EDEVICE. */
+int mpcd_get_state(mpcd_ctx* ctx, double* pos, double* vel, double* solute_pos,
+                   double* solute_vel, uint64_t* step);
+
+/* Same into device arrays of the storage type (float for MIXED, double for
+ * FP64), in input (tag) order.  Synchronises. */
+int mpcd_get_state_device(mpcd_ctx* ctx, void* pos, void* vel);
+
+/* Observables of the current state, computed on the device.  Synchronises. */
+int mpcd_observables(mpcd_ctx* ctx, mpcd_obs* out);
+
+/* Mean solvent v_x in nbins equal slabs of z in [0, n_z) (Poiseuille
+ * profile), computed on the device.  out: nbins doubles.  Synchronises. */
+int mpcd_profile(mpcd_ctx* ctx, int32_t nbins, double* out);
+
+/* Per-particle cell ids and per-cell member counts of the LAST completed
+ * step (diagnostics and tests).  cell_out: n_solvent + n_solute int32 in tag
+ * order (may be NULL); count_out: mpcd_num_cells entries (may be NULL).
+ * Synchronises. */
+int mpcd_last_cells(mpcd_ctx* ctx, int32_t* cell_out, int32_t* count_out);
+
+/* Internal profiler: advance nsteps SRD steps with plain launches and a CUDA
+ * event between phases; ms[i] receives the mean time of phase i per step
+ * (phases: md_bin, stream_bin, scan, scatter, permute, collide, end_step;
+ * see mpcd_phase_name).  nmax: capacity of ms (>= 7).  Synchronises.  The
+ * steps are real steps: the state advances. */
+int mpcd_phase_times(mpcd_ctx* ctx, int64_t nsteps, double* ms, int32_t nmax, int32_t* nphases);
+const char* mpcd_phase_name(int32_t i);
+
+/* Number of collision cells (n_z + 2 layers when walls_z is set). */
+int64_t mpcd_num_cells(const mpcd_ctx* ctx);
+
+/* Release everything.  NULL is allowed. */
+void mpcd_destroy(mpcd_ctx* ctx);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* mpcd_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Batched ensembles: many independent boxes advanced by the same launches */
+/* (one launch per phase covers every resident box).  Boxes differ in size, */
+/* density, rotation angle, seed and thermostat; one precision per batch.   */
+/* A box gives the same result alone and in any batch (counter-based draws  */
+/* keyed by the box's own seed, step and cell).                             */
+/* ---------------------------------------------------------------------- */
+typedef struct mpcd_batch mpcd_batch;
+
+/* Create an empty batch.  max_bytes: device-memory budget for admitted boxes
+ * (0 = no limit beyond the device).  Errors: EINVAL, ECUDA. */
+int mpcd_batch_create(int32_t precision, void* stream, int64_t max_bytes, mpcd_batch** out);
+
+/* Device bytes a box of these parameters and n_solvent particles occupies. */
+int64_t mpcd_box_footprint(const mpcd_params* params, int64_t n_solvent);
+
+/* Admit a box with its initial state (host arrays, as mpcd_set_state; no
+ * solute in batches).  *slot receives its handle.  Errors: EINVAL, ENOMEM
+ * (over the budget or the device), ECUDA. */
+int mpcd_batch_add(mpcd_batch* b, const mpcd_params* params, int64_t n_solvent,
+                   const double* pos, const double* vel, uint64_t step, int32_t* slot);
+
+/* Advance every resident box by nsteps.  Asynchronous like mpcd_step. */
+int mpcd_batch_step(mpcd_batch* b, int64_t nsteps);
+
+/* Copy one box's state out (tag order).  Synchronises. */
+int mpcd_batch_get_state(mpcd_batch* b, int32_t slot, double* pos, double* vel,
+                         uint64_t* step);
+
+/* Observables of one box.  Synchronises. */
+int mpcd_batch_observables(mpcd_batch* b, int32_t slot, mpcd_obs* out);
+
+/* Remove a box and free its memory. */
+int mpcd_batch_remove(mpcd_batch* b, int32_t slot);
+
+/* Number of resident boxes and device bytes they hold. */
+int mpcd_batch_info(const mpcd_batch* b, int32_t* n_boxes, int64_t* bytes_used);
+
+void mpcd_batch_destroy(mpcd_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

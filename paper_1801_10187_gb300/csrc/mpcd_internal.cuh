@@ -1,0 +1,134 @@
+// mpcd_internal.cuh -- device-side data layout and small device helpers of
+// libmpcd (SRD step of arXiv:1801.10187 on one GB300, sm_103a).
+//
+// Layout in HBM, per box (Sec. 3.2 particle data, re-laid for GB300):
+//   r, v      : packed xyz (3 x float in the mixed model, 3 x double in FP64),
+//               12 / 24 bytes per particle, no padding lane
+//   r2, v2    : second copies used by the periodic reorder (Sec. 3.8) and as
+//               scratch for tag-order output
+//   tag, tag2 : uint32 input index of the particle at each storage slot
+//   key       : uint64 (cell << 32 | slot-in-cell) written by binning
+//   order     : uint32 storage index of every sorted position (cell order)
+//   count     : uint32 per-cell histogram of the step (zeroed by the scan)
+//   start     : uint32 per-cell exclusive prefix sum, ncells + 1 entries
+// Solute beads (double) have their own short arrays; they are ordered per
+// collision tile rather than per cell.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpcd {
+
+// Random-stream purposes XORed into the high key word.
+constexpr uint32_t PURPOSE_SHIFT = 0x53484654u;
+constexpr uint32_t PURPOSE_ROT = 0x524F5441u;
+constexpr uint32_t PURPOSE_THERMO = 0x54484D4Fu;
+constexpr uint32_t PURPOSE_VIRT = 0x56495254u;
+
+// Error bits raised by kernels (read back by the host at sync points).
+constexpr int ERR_GAMMA_CAP = 1;   // thermostat sampler rejected 64 times
+constexpr int ERR_CELL_RANGE = 2;  // a cell id left the grid (non-finite position)
+
+constexpr int PTILE = 1024;    // particles per streaming / scatter tile
+constexpr int STILE = 2048;    // entries per scan tile
+constexpr int BLOCK = 256;     // threads per block of the tile kernels
+
+struct BoxDev {
+  // geometry and sizes
+  int32_t n[3];         // cells per axis
+  int32_t nzl;          // z layers of the collision grid (n_z, or n_z + 2 with walls)
+  int32_t ncells;       // n[0] * n[1] * nzl
+  int32_t nsol;         // solvent particles
+  int32_t nbead;        // solute beads
+  int32_t chain_len;
+  int32_t md_substeps;
+  int32_t thermostat;
+  int32_t walls;
+  int32_t sort_period;  // > 0: reorder when step % sort_period == 0
+  int32_t tc;           // cells per collision tile
+  int32_t nctiles;      // collision tiles of this box
+  uint32_t seed_lo, seed_hi;
+  // parameters, double
+  double dt, kT, m, Mb, bond_k, bond_r0, virt_density, sigma_virt;
+  double ca, sa, omc;   // cos(alpha), sin(alpha), 1 - cos(alpha)
+  double g[3], hg[3], gdt[3], L[3];
+  double md_h, md_hh;   // MD substep and half-kick factor (0.5 h) / M
+  // parameters, float (mixed model)
+  float dt_f, kT_f, m_f, Mb_f, ca_f, sa_f, omc_f, pad_f;
+  float g_f[3], hg_f[3], gdt_f[3], L_f[3];
+  // state; the pointers and counters below are updated on the device
+  void* r;
+  void* v;
+  void* r2;
+  void* v2;
+  uint32_t* tag;
+  uint32_t* tag2;
+  uint64_t* key;
+  uint32_t* order;
+  uint32_t* count;
+  uint32_t* start;
+  double* spos;
+  double* svel;
+  int32_t* bcell;   // bead cell id of the current step
+  uint64_t* bkey;   // bead (tile << 32 | slot)
+  uint32_t* border; // bead indices grouped by collision tile
+  uint32_t* bcount; // per collision tile bead histogram
+  uint32_t* bstart; // nctiles + 1
+  unsigned long long step;
+  int32_t permuted; // 1 if the last completed step reordered the particles
+  int32_t pad_i;
+};
+
+// Segments for the segmented exclusive scan (cells of each box, and bead
+// counts per collision tile of each box).
+struct ScanSeg {
+  uint32_t* count;
+  uint32_t* start;
+  int32_t n;
+  int32_t pad;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC11).  The 32x32->64 products
+// come from a 32-bit multiply (low half) and __umulhi (high half).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo_a = 0xD2511F53u * c.x;
+    const uint32_t hi_a = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo_b = 0xCD9E8D57u * c.z;
+    const uint32_t hi_b = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi_b ^ c.y ^ k.x, lo_b, hi_a ^ c.w ^ k.y, lo_a);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint2 box_key(const BoxDev& B, uint32_t purpose) {
+  return make_uint2(B.seed_lo, B.seed_hi ^ purpose);
+}
+
+__device__ __forceinline__ uint4 draw(const BoxDev& B, uint32_t purpose, uint32_t c0, uint32_t c1,
+                                      unsigned long long t) {
+  return philox(make_uint4(c0, c1, (uint32_t)t, (uint32_t)(t >> 32)), box_key(B, purpose));
+}
+
+// [0,1) from the top 53 bits of the 64-bit word (hi, lo).
+__device__ __forceinline__ double unit53(uint32_t hi, uint32_t lo) {
+  const unsigned long long x = ((unsigned long long)hi << 32) | lo;
+  return (double)(x >> 11) * 0x1p-53;
+}
+
+// Grid shift of step t, in units of 2^-32 cell edges: S in [-2^31, 2^31).
+__device__ __forceinline__ void shift_units(const BoxDev& B, unsigned long long t, long long S[3]) {
+  const uint4 w = draw(B, PURPOSE_SHIFT, 0xFFFFFFFFu, 0u, t);
+  S[0] = (long long)w.x - 2147483648LL;
+  S[1] = (long long)w.y - 2147483648LL;
+  S[2] = (long long)w.z - 2147483648LL;
+}
+
+constexpr double kTwoPi = 6.283185307179586;
+
+}  // namespace mpcd

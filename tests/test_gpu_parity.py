@@ -1,0 +1,283 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs, element by element.
+
+Tolerances (stated per model):
+  FP64  : cell ids and counts bit-exact; positions bit-exact for plain
+          streaming; velocities |dv| / max(|v|, sqrt(kT/m)) <= 1e-12.
+  mixed : bit-exact against the mixed-model oracle (cell ids, counts,
+          positions, velocities): both sides perform the same IEEE float and
+          int64 operations, including their own series sin/cos/log; with walls
+          the virtual-particle draws use double libm, so those runs compare to
+          2e-6.  Against the FP64 oracle from the same state: <= 1e-6 per step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_10187_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_1801_10187_gb300 as pkg  # noqa: E402
+
+
+def rel_err(v, ref, kT=1.0, m=1.0):
+    scale = np.maximum(np.linalg.norm(ref, axis=1), math.sqrt(kT / m))
+    return (np.linalg.norm(v - ref, axis=1) / scale).max(initial=0.0)
+
+
+def run_pair(n, rho, precision, steps=1, seed=5, step0=0, n_particles=None, oracle_precision=None,
+             **kw):
+    mixed = precision == "mixed"
+    s = inputs.solvent(n, rho, seed=seed, mixed=mixed, n_particles=n_particles)
+    box = pkg.Box(n=n, seed=seed, precision=precision, **kw)
+    box.set_state(s.pos, s.vel, step=step0)
+    box.step(steps)
+    pos, vel, _, _, st = box.get_state()
+    cells, counts = box.last_cells() if steps > 0 else (None, None)
+    op = oracle_precision if oracle_precision is not None else (oracle.MIXED if mixed else oracle.FP64)
+    okw = {k: v for k, v in kw.items() if k in ("thermostat", "walls_z", "g", "virt_density")}
+    if "body_force" in kw:
+        okw["g"] = kw["body_force"]
+    if "alpha_deg" in kw:
+        okw["alpha_deg"] = kw["alpha_deg"]
+    p = oracle.Params(n=n, seed=seed, precision=op, **okw)
+    ref = oracle.State(s.pos.copy(), s.vel.copy(), step=step0)
+    rc = oracle.step(p, ref, steps, want_cells=steps > 0)
+    box.close()
+    return pos, vel, st, cells, counts, ref, rc
+
+
+@pytest.mark.parametrize("thermostat", [False, True])
+def test_fp64_one_step_10cube(thermostat):
+    pos, vel, st, cells, counts, ref, (rc, rk) = run_pair((10, 10, 10), 5, "fp64",
+                                                          thermostat=thermostat)
+    assert st == ref.step == 1
+    assert np.array_equal(cells, rc)
+    assert np.array_equal(counts, rk)
+    assert np.array_equal(pos, ref.pos)
+    assert rel_err(vel, ref.vel) <= 1e-12
+
+
+@pytest.mark.parametrize("thermostat", [False, True])
+def test_mixed_one_step_10cube(thermostat):
+    pos, vel, st, cells, counts, ref, (rc, rk) = run_pair((10, 10, 10), 5, "mixed",
+                                                          thermostat=thermostat)
+    assert np.array_equal(cells, rc)
+    assert np.array_equal(counts, rk)
+    assert np.array_equal(pos, ref.pos)
+    assert np.array_equal(vel, ref.vel)
+
+
+@pytest.mark.parametrize("thermostat", [False, True])
+def test_mixed_against_fp64_oracle(thermostat):
+    pos, vel, st, cells, counts, ref, (rc, rk) = run_pair(
+        (10, 10, 10), 5, "mixed", thermostat=thermostat, oracle_precision=oracle.FP64)
+    assert np.array_equal(cells, rc)
+    assert rel_err(vel, ref.vel) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_ragged_sizes_many_tiles(precision):
+    # 23 x 17 x 9 cells, an odd particle count: several stream tiles and
+    # collision tiles with a ragged tail, and a start step off zero.
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    pos, vel, st, cells, counts, ref, (rc, rk) = run_pair(
+        (23, 17, 9), 7.3, precision, steps=3, thermostat=True, step0=123456789012,
+        n_particles=25699)
+    assert st == ref.step
+    assert np.array_equal(cells, rc)
+    assert np.array_equal(counts, rk)
+    if precision == "mixed":
+        assert np.array_equal(vel, ref.vel) and np.array_equal(pos, ref.pos)
+    assert rel_err(vel, ref.vel) <= tol * 3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_multi_step_trajectory_with_reorders(precision):
+    # 40 steps with a reorder every 7 steps: the trajectory still matches
+    # (bit for bit in the mixed model).
+    tol = 1e-11 if precision == "fp64" else 1e-5
+    pos, vel, st, cells, counts, ref, (rc, rk) = run_pair(
+        (12, 12, 12), 5, precision, steps=40, thermostat=True, sort_period=7, seed=9)
+    assert st == 40
+    assert np.array_equal(cells, rc)
+    if precision == "mixed":
+        assert np.array_equal(vel, ref.vel) and np.array_equal(pos, ref.pos)
+    assert rel_err(vel, ref.vel) <= tol
+    L = 12.0
+    d = np.abs(pos - ref.pos)
+    d = np.minimum(d, L - d)
+    assert d.max() <= (1e-11 if precision == "fp64" else 1e-4)
+
+
+def test_sort_period_does_not_change_mixed_results():
+    """Fixed-point cell sums are order independent: any reorder schedule gives
+    bit-identical trajectories."""
+    s = inputs.solvent((9, 8, 7), 6, seed=4, mixed=True)
+    outs = []
+    for sp in (-1, 1, 3, 25):
+        box = pkg.Box(n=(9, 8, 7), seed=4, precision="mixed", thermostat=True, sort_period=sp)
+        box.set_state(s.pos, s.vel)
+        box.step(15)
+        outs.append(box.get_state()[:2])
+        box.close()
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_walls_and_body_force(precision):
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    pos, vel, st, cells, counts, ref, (rc, rk) = run_pair(
+        (6, 5, 8), 10, precision, steps=4, thermostat=True, walls_z=True,
+        body_force=(0.01, 0.0, 0.0), virt_density=10.0, seed=13)
+    assert np.array_equal(cells, rc)
+    assert np.array_equal(counts, rk)
+    assert rel_err(vel, ref.vel) <= tol * 4
+    assert np.all((pos[:, 2] >= 0) & (pos[:, 2] < 8))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_clustered_input_takes_cooperative_path(precision):
+    """All particles in a few cells: tiles overflow the shared-memory capacity
+    and take the block-cooperative path; results still match."""
+    rng = np.random.default_rng(2)
+    N = 40000
+    pos = np.full((N, 3), 2.55) + rng.random((N, 3)) * 0.2  # the 0.2 wide cluster stays
+    pos[: N // 3, 0] += 3.0                                   # within one cell per axis
+    vel = rng.standard_normal((N, 3))
+    vel -= vel.mean(0)
+    if precision == "mixed":
+        pos = pos.astype(np.float32).astype(np.float64)
+        vel = vel.astype(np.float32).astype(np.float64)
+    box = pkg.Box(n=(8, 8, 8), seed=3, precision=precision, thermostat=True)
+    box.set_state(pos, vel)
+    box.step(1)  # one step: the cluster has not spread yet
+    p2, v2, *_ = box.get_state()
+    cells, counts = box.last_cells()
+    box.close()
+    ref = oracle.State(pos.copy(), vel.copy())
+    rc, rk = oracle.step(oracle.Params(n=(8, 8, 8), seed=3, thermostat=True,
+                                       precision=oracle.MIXED if precision == "mixed" else oracle.FP64),
+                         ref, 1, want_cells=True)
+    assert counts.max() > 4096  # above every tile capacity
+    assert np.array_equal(cells, rc)
+    assert rel_err(v2, ref.vel) <= (1e-12 if precision == "fp64" else 2e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_edge_cases_empty_single_and_one_cell_box(precision):
+    # empty state
+    box = pkg.Box(n=(3, 3, 3), precision=precision)
+    box.set_state(np.zeros((0, 3)), np.zeros((0, 3)))
+    box.step(3)
+    pos, vel, *_ , st = box.get_state()
+    assert pos.shape == (0, 3) and st == 3
+    box.close()
+    # a single particle keeps its velocity (to rounding) and streams
+    box = pkg.Box(n=(3, 3, 3), precision=precision, seed=2)
+    box.set_state(np.array([[1.5, 1.5, 1.5]]), np.array([[0.5, -0.25, 1.0]]))
+    box.step(4)
+    pos, vel, *_ = box.get_state()
+    assert np.allclose(vel, [[0.5, -0.25, 1.0]], atol=1e-6)
+    assert np.allclose(pos, [[1.7, 1.4, 1.9]], atol=1e-5)
+    box.close()
+    # a 1 x 1 x 1 box: one cell, every particle collides with all others
+    s = inputs.solvent((1, 1, 1), 50, seed=8, mixed=precision == "mixed")
+    box = pkg.Box(n=(1, 1, 1), precision=precision, seed=8, thermostat=True)
+    box.set_state(s.pos, s.vel)
+    box.step(5)
+    _, vel, *_ = box.get_state()
+    box.close()
+    ref = oracle.State(s.pos.copy(), s.vel.copy())
+    oracle.step(oracle.Params(n=(1, 1, 1), seed=8, thermostat=True,
+                              precision=oracle.MIXED if precision == "mixed" else oracle.FP64), ref, 5)
+    assert rel_err(vel, ref.vel) <= (1e-12 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solute_chains(precision):
+    n = (8, 8, 8)
+    s = inputs.solvent(n, 5, seed=21, mixed=precision == "mixed")
+    sp, sv = inputs.chains(n, 6, 10, 0.5, bead_mass=5.0, seed=22)
+    kw = dict(chain_len=10, md_substeps=10, solute_mass=5.0, bond_k=1000.0, bond_r0=0.5)
+    box = pkg.Box(n=n, seed=21, precision=precision, thermostat=True, **kw)
+    box.set_state(s.pos, s.vel, sp, sv)
+    box.step(3)
+    pos, vel, spos, svel, st = box.get_state()
+    cells, counts = box.last_cells()
+    box.close()
+    p = oracle.Params(n=n, seed=21, thermostat=True,
+                      precision=oracle.MIXED if precision == "mixed" else oracle.FP64, **kw)
+    ref = oracle.State(s.pos.copy(), s.vel.copy(), sp.copy(), sv.copy())
+    rc, rk = oracle.step(p, ref, 3, want_cells=True)
+    assert np.array_equal(cells, rc)
+    assert np.array_equal(counts, rk)
+    tol = 1e-11 if precision == "fp64" else 3e-6
+    assert rel_err(vel, ref.vel) <= tol
+    assert rel_err(svel, ref.svel, m=5.0) <= tol
+    assert np.max(np.abs(spos - ref.spos)) <= 1e-11
+
+
+def test_observables_match_oracle():
+    s = inputs.solvent((10, 10, 10), 10, seed=6)
+    box = pkg.Box(n=(10, 10, 10), seed=6, precision="fp64", thermostat=True)
+    box.set_state(s.pos, s.vel)
+    box.step(5)
+    ob = box.observables()
+    pos, vel, *_ = box.get_state()
+    box.close()
+    ref = oracle.observables(oracle.Params(n=(10, 10, 10)), oracle.State(pos, vel))
+    assert np.allclose(ob["P"], ref["P"], atol=1e-9)
+    assert abs(ob["KE"] - ref["KE"]) <= 1e-10 * ref["KE"]
+    assert abs(ob["T_kin"] - ref["T_kin"]) <= 1e-10
+    assert abs(ob["T_cell_mean"] - ref["T_cell_mean"]) <= 1e-8
+    assert ob["occupied_cells"] == ref["occupied_cells"]
+    assert ob["step"] == 5
+
+
+def test_batch_boxes_equal_alone():
+    """Boxes of different size, density, angle and seed stepped together give
+    bit-identical results to each box alone (mixed model)."""
+    specs = [((12, 9, 7), 5, 90.0, 101), ((5, 5, 5), 10, 120.0, 102), ((16, 16, 16), 5, 130.0, 103)]
+    states = [inputs.solvent(n, rho, seed=sd, mixed=True) for n, rho, _, sd in specs]
+    batch = pkg.Batch("mixed")
+    slots = []
+    for (n, rho, ang, sd), s in zip(specs, states):
+        slots.append(batch.add(s.pos, s.vel, n=n, alpha_deg=ang, seed=sd, thermostat=(sd % 2 == 1)))
+    batch.step(6)
+    got = [batch.get_state(sl) for sl in slots]
+    # remove the middle box and keep stepping the others
+    batch.remove(slots[1])
+    batch.step(4)
+    got_after = [batch.get_state(slots[0]), batch.get_state(slots[2])]
+    batch.close()
+    for (n, rho, ang, sd), s, g in zip(specs, states, got):
+        box = pkg.Box(n=n, alpha_deg=ang, seed=sd, thermostat=(sd % 2 == 1), precision="mixed")
+        box.set_state(s.pos, s.vel)
+        box.step(6)
+        pos, vel, *_ = box.get_state()
+        assert np.array_equal(pos, g[0]) and np.array_equal(vel, g[1]) and g[2] == 6
+        if sd != 102:
+            box.step(4)
+            pos, vel, *_ = box.get_state()
+            ga = got_after[0 if sd == 101 else 1]
+            assert np.array_equal(pos, ga[0]) and np.array_equal(vel, ga[1]) and ga[2] == 10
+        box.close()
+
+
+def test_invalid_arguments_raise():
+    with pytest.raises(pkg.MpcdError):
+        pkg.Box(n=(0, 4, 4))
+    box = pkg.Box(n=(4, 4, 4))
+    with pytest.raises(pkg.MpcdError) as e:
+        box.step(1)
+    assert e.value.code == pkg.MPCD_ESTATE
+    box.close()
