@@ -281,3 +281,21 @@ def test_invalid_arguments_raise():
         box.step(1)
     assert e.value.code == pkg.MPCD_ESTATE
     box.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_profile_matches_oracle(precision):
+    """mpcd_profile (mean solvent v_x per z slab) against the oracle's profile of
+    the same state, in a body-force channel."""
+    n = (6, 5, 12)
+    s = inputs.solvent(n, 10, seed=17, mixed=precision == "mixed")
+    box = pkg.Box(n=n, seed=17, precision=precision, thermostat=True, walls_z=True,
+                  body_force=(0.02, 0.0, 0.0), virt_density=10.0)
+    box.set_state(s.pos, s.vel)
+    box.step(30)
+    prof = box.profile(24)
+    pos, vel, *_ = box.get_state()
+    box.close()
+    ref = oracle.profile(oracle.Params(n=n), oracle.State(pos, vel), 24)
+    assert np.allclose(prof, ref, rtol=0, atol=1e-12)
+    assert prof[12] > 0.0  # the body force drives +x flow in the middle of the channel
