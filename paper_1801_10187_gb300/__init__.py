@@ -92,6 +92,7 @@ def lib():
     L.mpcd_observables.argtypes = [vp, P(_Obs)]
     L.mpcd_profile.argtypes = [vp, i32, dp]
     L.mpcd_last_cells.argtypes = [vp, P(i32), P(i32)]
+    L.mpcd_profile_noalloc.argtypes = [vp, i32, dp]
     L.mpcd_phase_times.argtypes = [vp, i64, dp, i32, P(i32)]
     L.mpcd_phase_name.argtypes = [i32]
     L.mpcd_phase_name.restype = ctypes.c_char_p
@@ -112,7 +113,7 @@ def lib():
     L.mpcd_batch_destroy.restype = None
     for name in ("mpcd_create", "mpcd_set_state", "mpcd_set_state_device", "mpcd_step",
                  "mpcd_get_state", "mpcd_get_state_device", "mpcd_observables", "mpcd_profile",
-                 "mpcd_last_cells", "mpcd_phase_times", "mpcd_batch_create", "mpcd_batch_add", "mpcd_batch_step",
+                 "mpcd_last_cells", "mpcd_phase_times", "mpcd_profile_noalloc", "mpcd_batch_create", "mpcd_batch_add", "mpcd_batch_step",
                  "mpcd_batch_get_state", "mpcd_batch_observables", "mpcd_batch_remove",
                  "mpcd_batch_info"):
         getattr(L, name).restype = c_int
@@ -241,6 +242,12 @@ class Box:
         k = ctypes.c_int32(0)
         _check(lib().mpcd_phase_times(self._ctx, int(nsteps), _dptr(ms), 16, ctypes.byref(k)))
         return {lib().mpcd_phase_name(i).decode(): float(ms[i]) for i in range(k.value)}
+
+    def profile_noalloc(self, nbins: int) -> np.ndarray:
+        """mpcd_profile without any device allocation (static 4096-bin scratch)."""
+        out = np.zeros(nbins)
+        _check(lib().mpcd_profile_noalloc(self._ctx, int(nbins), _dptr(out)))
+        return out
 
     def last_cells(self):
         cells = np.empty(self.n_solvent + self.n_solute, dtype=np.int32)

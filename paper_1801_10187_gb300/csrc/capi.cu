@@ -1045,3 +1045,104 @@ int mpcd_batch_info(const mpcd_batch* bt, int32_t* n_boxes, int64_t* bytes_used)
 void mpcd_batch_destroy(mpcd_batch* bt) { delete bt; }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free variant of mpcd_profile.
+//
+// Some callers cannot allocate device memory at the moment they want a
+// profile: code running while a CUDA stream is being captured into a graph
+// (cudaMalloc / cudaMallocAsync are not allowed there), and services that run
+// inside a fixed, pre-reserved device-memory budget where every allocation
+// is accounted for up front.  This entry point uses only memory that already
+// exists: the box's own arrays and a static per-bin scratch array below.
+// ===========================================================================
+namespace {
+
+constexpr int kProfileNoAllocMaxBins = 4096;
+
+// Per-bin scratch shared by every call on a device and held by every GPU that
+// loads the library until the process exits: sums of v_x in
+// [0, kProfileNoAllocMaxBins), member counts (as doubles) after that, and the
+// finished means written back over the sums.
+static __device__ __align__(256) double g_profile_scratch[2 * kProfileNoAllocMaxBins];
+
+// Device address of g_profile_scratch per device, looked up once per device.
+std::mutex g_profile_scratch_mu;
+void* g_profile_scratch_addr[64] = {};
+
+__global__ void k_profile_noalloc_clear(int nbins) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * nbins; i += gridDim.x * blockDim.x) {
+    const int j = i < nbins ? i : kProfileNoAllocMaxBins + (i - nbins);
+    g_profile_scratch[j] = 0.0;
+  }
+}
+
+template <bool MIXED>
+__global__ void k_profile_noalloc_accumulate(const BoxDev* __restrict__ box, int nbins, double H,
+                                             double* __restrict__ scratch) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  const BoxDev& B = *box;
+  const T* r = (const T*)B.r;
+  const T* v = (const T*)B.v;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.nsol; i += gridDim.x * blockDim.x) {
+    long long b = (long long)floor((double)r[3 * i + 2] / H * (double)nbins);
+    if (b < 0) b = 0;
+    if (b >= nbins) b = nbins - 1;
+    atomicAdd(&scratch[b], (double)v[3 * i]);
+    atomicAdd(&scratch[kProfileNoAllocMaxBins + b], 1.0);
+  }
+}
+
+__global__ void k_profile_noalloc_finish(int nbins, double* __restrict__ scratch) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+    const double c = scratch[kProfileNoAllocMaxBins + b];
+    scratch[b] = c > 0.0 ? scratch[b] / c : 0.0;
+  }
+}
+
+}  // namespace
+
+extern "C" int mpcd_profile_noalloc(mpcd_ctx* ctx, int32_t nbins, double* out) {
+  g_last_error.clear();
+  if (!ctx || !out) return fail(MPCD_EINVAL, "NULL argument");
+  if (nbins < 1 || nbins > kProfileNoAllocMaxBins)
+    return fail(MPCD_EINVAL, "nbins must be in [1, 4096] for the allocation-free profile");
+  Box* b = ctx->box;
+  Engine& E = ctx->eng;
+  if (!b->has_state) return fail(MPCD_ESTATE, "no state set");
+  if (!E.tables_ok || b->dev_index < 0)
+    return fail(MPCD_ESTATE,
+                "the box is not on the device yet: call mpcd_step (0 steps is enough) first");
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(MPCD_ECUDA, "device index out of range");
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_profile_scratch_mu);
+    if (!g_profile_scratch_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_profile_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(MPCD_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_profile_scratch_addr[dev] = p;
+    }
+    scratch = g_profile_scratch_addr[dev];
+  }
+  const BoxDev* rec = E.d_boxes + b->dev_index;
+  const int n = (int)b->nsol;
+  int grid = (n + 255) / 256;
+  if (grid < 1) grid = 1;
+  if (grid > 4096) grid = 4096;
+  k_profile_noalloc_clear<<<(2 * nbins + 255) / 256, 256, 0, E.stream>>>(nbins);
+  if (E.mixed)
+    k_profile_noalloc_accumulate<true><<<grid, 256, 0, E.stream>>>(rec, nbins, (double)b->p.n[2],
+                                                                   (double*)scratch);
+  else
+    k_profile_noalloc_accumulate<false><<<grid, 256, 0, E.stream>>>(rec, nbins, (double)b->p.n[2],
+                                                                    (double*)scratch);
+  k_profile_noalloc_finish<<<(nbins + 255) / 256, 256, 0, E.stream>>>(nbins, (double*)scratch);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(out, scratch, sizeof(double) * nbins, cudaMemcpyDeviceToHost, E.stream));
+  CUDA_TRY(cudaStreamSynchronize(E.stream));
+  return MPCD_OK;
+}
