@@ -40,10 +40,10 @@ from paper_1801_10187_gb300 import inputs  # noqa: E402
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "MPCD particle-steps/s"
 UNIT = "particle-steps/s"
-# kernels launched per step (stream_bin, 3 scan phases, scatter, permute, swap,
-# collide, end_step); the solute adds md_bin, 3 bead-scan phases, bead scatter
-LAUNCHES_PER_STEP = 9
-LAUNCHES_PER_STEP_SOLUTE = 14
+# kernels launched per step: the fused cell kernel and the record update; the
+# solute adds MD + bead grouping, 3 bead-scan phases and the bead scatter
+LAUNCHES_PER_STEP = 2
+LAUNCHES_PER_STEP_SOLUTE = 7
 
 
 def load_peaks():
@@ -292,17 +292,17 @@ def main():
     phases = box.phase_times(min(K, 50))
     hbm_peak, peak_src = load_peaks()
     es = 4 if cfg["precision"] == "mixed" else 8
-    alg = {"stream_bin": (2 * 3 * es + 3 * es) * s.pos.shape[0],   # read r, v; write r
-           "collide": (2 * 3 * es) * s.pos.shape[0]}                # read v; write v
-    dom = max(("stream_bin", "collide"), key=lambda k: phases.get(k, 0.0))
+    # the fused kernel performs the whole step: its algorithmic bytes are the
+    # step's, 2 s_r + 3 s_v per particle (read r, write r, read v twice, write v)
+    step_bytes = 2 * 3 * es + 3 * 3 * es
+    dom = "fused_step"
     dom_ms = phases[dom]
-    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9
-    traffic = kernel_traffic(dom, args.workload)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-                "peak_source": peak_src,
-                "alg_bytes_per_particle": alg[dom] / s.pos.shape[0]}
-    step_bytes = (2 * 3 * es + 3 * 3 * es)  # 2 s_r + 3 s_v per particle-step
+    achieved = step_bytes * s.pos.shape[0] / (dom_ms * 1e-3) / 1e9
+    traffic = kernel_traffic("k_cells", args.workload)
+    roofline = {"bound": "hbm", "kernel": "k_cells (collide t + stream/bin t+1)",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
+                "alg_bytes_per_particle": step_bytes}
     step_gbs = step_bytes * N * K / (ms * 1e-3) / 1e9 / world
     hbm_step = {"bytes_per_particle_step": step_bytes, "achieved_gbs": step_gbs,
                 "frac_of_peak": step_gbs / hbm_peak, "frac_of_8tbs": step_gbs / 8000.0,

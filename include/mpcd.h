@@ -108,6 +108,12 @@ int mpcd_set_state(mpcd_ctx* ctx, int64_t n_solvent, const double* pos, const do
 int mpcd_set_state_device(mpcd_ctx* ctx, int64_t n_solvent, const void* pos, const void* vel,
                           uint64_t step);
 
+/* Thermal initial state drawn on the device (input generation, Sec. 4 /
+ * Sec. 4.1 set-up): positions uniform in the box, velocity components
+ * Gaussian with variance kT/m, mean velocity removed; reproducible from
+ * init_seed.  No solute.  Synchronises.  Errors: EINVAL, ENOMEM, ECUDA. */
+int mpcd_set_state_thermal(mpcd_ctx* ctx, int64_t n_solvent, uint64_t init_seed, uint64_t step);
+
 /* Advance nsteps SRD steps.  Enqueued on the context's stream (replays of a
  * captured CUDA graph); returns without synchronising.  A device-side limit
  * hit during these steps is reported by the next synchronising call.
@@ -192,6 +198,11 @@ int64_t mpcd_box_footprint(const mpcd_params* params, int64_t n_solvent);
 int mpcd_batch_add(mpcd_batch* b, const mpcd_params* params, int64_t n_solvent,
                    const double* pos, const double* vel, uint64_t step, int32_t* slot);
 
+/* Admit a box with a thermal initial state drawn on the device (as
+ * mpcd_set_state_thermal). */
+int mpcd_batch_add_thermal(mpcd_batch* b, const mpcd_params* params, int64_t n_solvent,
+                           uint64_t init_seed, uint64_t step, int32_t* slot);
+
 /* Advance every resident box by nsteps.  Asynchronous like mpcd_step. */
 int mpcd_batch_step(mpcd_batch* b, int64_t nsteps);
 
@@ -204,6 +215,10 @@ int mpcd_batch_observables(mpcd_batch* b, int32_t slot, mpcd_obs* out);
 
 /* Remove a box and free its memory. */
 int mpcd_batch_remove(mpcd_batch* b, int32_t slot);
+
+/* Wait until the batch's queued work is done; reports device-side limits
+ * hit meanwhile (MPCD_EDEVICE). */
+int mpcd_batch_sync(mpcd_batch* b);
 
 /* Number of resident boxes and device bytes they hold. */
 int mpcd_batch_info(const mpcd_batch* b, int32_t* n_boxes, int64_t* bytes_used);

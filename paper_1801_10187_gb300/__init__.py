@@ -86,6 +86,8 @@ def lib():
     L.mpcd_create.argtypes = [P(_Params), vp, P(vp)]
     L.mpcd_set_state.argtypes = [vp, i64, dp, dp, i64, dp, dp, u64]
     L.mpcd_set_state_device.argtypes = [vp, i64, vp, vp, u64]
+    L.mpcd_set_state_thermal.argtypes = [vp, i64, u64, u64]
+    L.mpcd_batch_add_thermal.argtypes = [vp, P(_Params), i64, u64, u64, P(i32)]
     L.mpcd_step.argtypes = [vp, i64]
     L.mpcd_get_state.argtypes = [vp, dp, dp, dp, dp, P(u64)]
     L.mpcd_get_state_device.argtypes = [vp, vp, vp]
@@ -109,13 +111,15 @@ def lib():
     L.mpcd_batch_observables.argtypes = [vp, i32, P(_Obs)]
     L.mpcd_batch_remove.argtypes = [vp, i32]
     L.mpcd_batch_info.argtypes = [vp, P(i32), P(i64)]
+    L.mpcd_batch_sync.argtypes = [vp]
     L.mpcd_batch_destroy.argtypes = [vp]
     L.mpcd_batch_destroy.restype = None
     for name in ("mpcd_create", "mpcd_set_state", "mpcd_set_state_device", "mpcd_step",
+                 "mpcd_set_state_thermal", "mpcd_batch_add_thermal",
                  "mpcd_get_state", "mpcd_get_state_device", "mpcd_observables", "mpcd_profile",
                  "mpcd_last_cells", "mpcd_phase_times", "mpcd_profile_noalloc", "mpcd_batch_create", "mpcd_batch_add", "mpcd_batch_step",
                  "mpcd_batch_get_state", "mpcd_batch_observables", "mpcd_batch_remove",
-                 "mpcd_batch_info"):
+                 "mpcd_batch_info", "mpcd_batch_sync"):
         getattr(L, name).restype = c_int
     _lib_handle = L
     return L
@@ -208,6 +212,13 @@ class Box:
         _check(lib().mpcd_set_state_device(self._ctx, int(pos.shape[0]), ctypes.c_void_p(pos.data_ptr()),
                                            ctypes.c_void_p(vel.data_ptr()), int(step)))
 
+    def set_state_thermal(self, n_solvent: int, init_seed: int, step=0):
+        """Thermal initial state drawn on the device (uniform positions, Gaussian
+        velocities of variance kT/m, zero total momentum)."""
+        self.n_solvent, self.n_solute = int(n_solvent), 0
+        _check(lib().mpcd_set_state_thermal(self._ctx, int(n_solvent), int(init_seed) & (2**64 - 1),
+                                            int(step)))
+
     def step(self, nsteps=1):
         _check(lib().mpcd_step(self._ctx, int(nsteps)))
 
@@ -294,6 +305,17 @@ class Batch:
         self.sizes[slot.value] = pos.shape[0]
         return slot.value
 
+    def add_thermal(self, n_solvent: int, init_seed: int, step=0, **kw) -> int:
+        """Admit a box whose thermal initial state is drawn on the device."""
+        kw.setdefault("precision", "mixed" if self.precision == MIXED else "fp64")
+        p = make_params(**kw)
+        slot = ctypes.c_int32(-1)
+        _check(lib().mpcd_batch_add_thermal(self._b, ctypes.byref(p), int(n_solvent),
+                                            int(init_seed) & (2**64 - 1), int(step),
+                                            ctypes.byref(slot)))
+        self.sizes[slot.value] = int(n_solvent)
+        return slot.value
+
     def step(self, nsteps=1):
         _check(lib().mpcd_batch_step(self._b, int(nsteps)))
 
@@ -312,6 +334,9 @@ class Batch:
     def remove(self, slot: int):
         _check(lib().mpcd_batch_remove(self._b, int(slot)))
         self.sizes.pop(slot, None)
+
+    def sync(self):
+        _check(lib().mpcd_batch_sync(self._b))
 
     def info(self):
         n = ctypes.c_int32(0)

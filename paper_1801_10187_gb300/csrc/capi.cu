@@ -2,16 +2,24 @@
 //
 // An Engine holds one or more independent boxes of one precision.  Each box
 // owns its device arrays (stream-ordered allocations); a host-built table of
-// BoxDev records plus tile tables lets every kernel launch cover all boxes.
-// One step is captured once into a CUDA graph and replayed; the graph is
-// re-captured only when the set of boxes changes.  Step counters and the
-// buffer swaps of the periodic reorder live in the device records, so graph
-// replays need no host involvement.
+// BoxDev records plus span tables (256 cells per span, one list per kernel
+// variant) lets every launch cover all boxes.
+//
+// Stepping.  One fused pass per step (k_cells, mode F) collides step t and
+// streams and bins step t + 1.  The state therefore rests "half a step on":
+// after mpcd_step the last collision is still pending.  Reading the state (or
+// changing the set of boxes) first completes it (mode C, in place); stepping
+// from a completed state first streams and bins (mode P).  Consecutive
+// mpcd_step calls thus cost exactly one pass per step.  The P, F and C passes
+// are each captured once into a CUDA graph and replayed; step counters and the
+// buffer flips live in the device records.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mpcd.h"
@@ -39,50 +47,37 @@ int fail(int code, const std::string& msg) {
     }                                                                                      \
   } while (0)
 
-constexpr int CAP_MIXED = 2048;  // shared-memory particle capacity of a collision tile
-constexpr int CAP_FP64 = 1536;
-constexpr int BCAP = 128;        // beads per collision tile on the fast path
-
-struct Box {
-  mpcd_params p{};
-  int64_t nsol = 0, nbead = 0;
-  BoxDev d{};                  // host mirror of the device record
-  std::vector<void*> allocs;   // device allocations of this box
-  size_t bytes = 0;
-  bool has_state = false;
-  int dev_index = -1;          // index in the device table, -1 if not uploaded
-  // observables scratch (allocated lazily)
-  void* obs = nullptr;
-  size_t obs_bytes = 0;
-};
-
 size_t elem_size(bool mixed) { return mixed ? sizeof(float) : sizeof(double); }
+size_t rec_size(bool mixed) { return mixed ? sizeof(RecF) : sizeof(RecD); }
 
 int64_t cells_of(const mpcd_params& p) {
   return (int64_t)p.n[0] * p.n[1] * (p.n[2] + (p.walls_z ? 2 : 0));
 }
 
-int choose_tc(bool mixed, int64_t nsol, int64_t ncells) {
-  const int cap = mixed ? CAP_MIXED : CAP_FP64;
-  const double rho = ncells > 0 ? (double)nsol / (double)ncells : 0.0;
-  int tc = rho > 0.0 ? (int)std::floor((double)cap / (2.0 * rho)) : BLOCK;
-  if (tc > BLOCK) tc = BLOCK;
-  if (tc < 1) tc = 1;
-  return tc;
+// Records per cell row: the mean occupancy plus six standard deviations of a
+// Poisson count and a margin, rounded up to a multiple of 4.  Busier cells
+// spill into the overflow list, which stays correct for any input.
+int row_capacity(const mpcd_params& p, int64_t nsol) {
+  const double V = (double)p.n[0] * p.n[1] * p.n[2];
+  const double rho = V > 0 ? (double)nsol / V : 0.0;
+  int K = (int)std::ceil(rho + 6.0 * std::sqrt(rho) + 4.0);
+  if (K < 8) K = 8;
+  return (K + 3) & ~3;
 }
 
 size_t footprint_bytes(const mpcd_params& p, int64_t nsol, int64_t nbead) {
   const bool mixed = p.precision == MPCD_MIXED;
-  const size_t es = elem_size(mixed);
   const int64_t C = cells_of(p);
-  const int tc = choose_tc(mixed, nsol, C);
-  const int64_t nct = (C + tc - 1) / tc;
+  const int K = row_capacity(p, nsol);
+  const int64_t ng = (C + BEAD_TILE - 1) / BEAD_TILE;
   size_t b = 0;
-  b += (size_t)nsol * (4 * 3 * es + 2 * sizeof(uint32_t) + sizeof(uint64_t) + sizeof(uint32_t));
-  b += (size_t)C * sizeof(uint32_t) + (size_t)(C + 1) * sizeof(uint32_t);
+  b += 2 * (size_t)C * K * rec_size(mixed);                               // rows
+  b += 2 * (size_t)C * sizeof(uint32_t);                                  // counts
+  b += 2 * (size_t)std::max<int64_t>(nsol, 1) * (rec_size(mixed) + 4);     // overflow lists
+  b += (size_t)nsol * 6 * elem_size(mixed);                               // staging (r, v)
   if (nbead > 0) {
     b += (size_t)nbead * (6 * sizeof(double) + sizeof(int32_t) + sizeof(uint64_t) + sizeof(uint32_t));
-    b += (size_t)nct * sizeof(uint32_t) + (size_t)(nct + 1) * sizeof(uint32_t);
+    b += (size_t)ng * sizeof(uint32_t) + (size_t)(ng + 1) * sizeof(uint32_t);
   }
   return b;
 }
@@ -108,9 +103,22 @@ int validate(const mpcd_params* p, int precision_expected) {
     return fail(MPCD_EINVAL, "solute needs md_substeps >= 1 and solute_mass > 0");
   const int64_t C = cells_of(*p);
   if (C > 2000000000LL) return fail(MPCD_EINVAL, "too many cells (max 2e9)");
-  if ((int64_t)p->n[0] * p->n[1] > 65535LL * 65535LL) return fail(MPCD_EINVAL, "grid too large");
   return MPCD_OK;
 }
+
+struct Box {
+  mpcd_params p{};
+  int64_t nsol = 0, nbead = 0;
+  BoxDev d{};                  // host mirror of the device record
+  std::vector<void*> allocs;   // device allocations of this box
+  size_t bytes = 0;
+  bool has_state = false;
+  int dev_index = -1;          // index in the device table, -1 if not uploaded
+  void* stage_r = nullptr;     // n x 3 staging arrays (input order)
+  void* stage_v = nullptr;
+  void* obs = nullptr;         // observables scratch (allocated lazily)
+  size_t obs_bytes = 0;
+};
 
 }  // namespace
 
@@ -123,20 +131,13 @@ struct Engine {
   int64_t max_bytes = 0;
   size_t used_bytes = 0;
   std::vector<Box*> slots;
-  std::vector<Box*> live;  // boxes in the device table, in table order
+  std::vector<Box*> live;  // boxes in the device table
 
   // device tables
   BoxDev* d_boxes = nullptr;
   int n_records = 0;
-  int2* d_ptiles = nullptr;
-  int n_ptiles = 0;
-  int2* d_ctiles[4] = {nullptr, nullptr, nullptr, nullptr};  // per collide variant
-  int n_ctiles[4] = {0, 0, 0, 0};
-  int2* d_ovf = nullptr;  // overflow queue of collision tiles
-  int* d_novf = nullptr;
-  ScanSeg* d_csegs = nullptr;
-  int2* d_cstiles = nullptr;
-  int n_cstiles = 0;
+  int2* d_spans[4] = {nullptr, nullptr, nullptr, nullptr};  // per kernel variant
+  int n_spans[4] = {0, 0, 0, 0};
   ScanSeg* d_bsegs = nullptr;
   int2* d_bstiles = nullptr;
   int n_bstiles = 0;
@@ -148,18 +149,14 @@ struct Engine {
   uint32_t* d_tsum = nullptr;
   unsigned long long* d_gscan = nullptr;
   uint32_t* d_toff = nullptr;
-  int scan_capacity = 0;
   int* d_err = nullptr;
   double* d_partials = nullptr;
   bool any_beads = false;
+  int cells_bps[3][4] = {};
 
-  int cap = CAP_MIXED, bcap = BCAP;
-  size_t collide_smem = 0;
-  int collide_bps[4] = {1, 1, 1, 1};
-
-  cudaGraphExec_t gexec = nullptr;
-  bool graph_ok = false;
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // MODE_P, MODE_F, MODE_C
   bool tables_ok = false;
+  bool pending = false;  // the last collision of every live box is still to do
 
   int init(int precision, void* user_stream) {
     mixed = precision == MPCD_MIXED;
@@ -173,17 +170,13 @@ struct Engine {
       CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
       own_stream = true;
     }
-    cap = mixed ? CAP_MIXED : CAP_FP64;
-    collide_smem = collide_smem_bytes(mixed, cap, bcap);
-    CUDA_TRY(prepare_collide(mixed, collide_smem));
-    for (int v = 0; v < 4; ++v) {
-      collide_bps[v] = collide_blocks_per_sm(mixed, v, collide_smem);
-      if (collide_bps[v] < 1) collide_bps[v] = 1;
-    }
+    for (int m = 0; m < 3; ++m)
+      for (int v = 0; v < 4; ++v) {
+        cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
+        if (cells_bps[m][v] < 1) cells_bps[m][v] = 1;
+      }
     CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
     CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
-    CUDA_TRY(cudaMalloc(&d_novf, sizeof(int)));
-    CUDA_TRY(cudaMemsetAsync(d_novf, 0, sizeof(int), stream));
     CUDA_TRY(cudaMalloc(&d_partials, sizeof(double) * 4 * 4096));
     // keep freed box memory cached in the pool for quick re-admission
     cudaMemPool_t pool;
@@ -195,50 +188,54 @@ struct Engine {
   }
 
   void free_tables() {
-    void* ptrs[] = {d_boxes, d_ptiles, d_ctiles[0], d_ctiles[1], d_ctiles[2], d_ctiles[3],
-                    d_ovf, d_csegs, d_cstiles, d_bsegs, d_bstiles, d_btiles, d_mdtiles, d_tsum,
-                    d_gscan, d_toff};
+    void* ptrs[] = {d_boxes, d_spans[0], d_spans[1], d_spans[2], d_spans[3], d_bsegs, d_bstiles,
+                    d_btiles, d_mdtiles, d_tsum, d_gscan, d_toff};
     for (void* q : ptrs)
       if (q) cudaFree(q);
     for (int v = 0; v < 4; ++v) {
-      d_ctiles[v] = nullptr;
-      n_ctiles[v] = 0;
+      d_spans[v] = nullptr;
+      n_spans[v] = 0;
     }
-    d_ovf = nullptr;
-    d_boxes = nullptr; d_ptiles = nullptr; d_csegs = nullptr;
-    d_cstiles = nullptr; d_bsegs = nullptr; d_bstiles = nullptr; d_btiles = nullptr;
+    d_boxes = nullptr; d_bsegs = nullptr; d_bstiles = nullptr; d_btiles = nullptr;
     d_mdtiles = nullptr; d_tsum = nullptr; d_gscan = nullptr; d_toff = nullptr;
-    scan_capacity = 0;
     n_records = 0;
   }
 
-  void drop_graph() {
-    if (gexec) cudaGraphExecDestroy(gexec);
-    gexec = nullptr;
-    graph_ok = false;
+  void drop_graphs() {
+    for (auto& g : gexec) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
   }
 
   ~Engine() {
     if (stream) cudaStreamSynchronize(stream);
-    drop_graph();
+    drop_graphs();
     for (Box* b : slots) release_box(b);
     free_tables();
     if (d_err) cudaFree(d_err);
-    if (d_novf) cudaFree(d_novf);
     if (d_partials) cudaFree(d_partials);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
 
-  void release_box(Box* b) {
-    if (!b) return;
+  void free_box_arrays(Box* b) {
     for (void* q : b->allocs)
       if (q) cudaFreeAsync(q, stream);
+    b->allocs.clear();
     if (b->obs) cudaFreeAsync(b->obs, stream);
+    b->obs = nullptr;
+    b->obs_bytes = 0;
+    b->stage_r = b->stage_v = nullptr;
     used_bytes -= b->bytes;
+    b->bytes = 0;
+  }
+
+  void release_box(Box* b) {
+    if (!b) return;
+    free_box_arrays(b);
     delete b;
   }
 
-  // Bring the host mirrors up to date with the device records.
   int pull_records() {
     if (!d_boxes || live.empty() || n_records == 0) return MPCD_OK;
     std::vector<BoxDev> rec(n_records);
@@ -250,7 +247,7 @@ struct Engine {
     return MPCD_OK;
   }
 
-  // Forget a box that is about to be freed or re-set (after pull_records).
+  // Forget a box that is about to be freed or re-set (state must be complete).
   void unlink(Box* b) {
     for (size_t i = 0; i < live.size(); ++i)
       if (live[i] == b) {
@@ -258,7 +255,7 @@ struct Engine {
         break;
       }
     b->dev_index = -1;
-    drop_graph();
+    drop_graphs();
     tables_ok = false;
   }
 
@@ -271,16 +268,16 @@ struct Engine {
       std::string m;
       if (h & ERR_GAMMA_CAP) m += "thermostat Gamma sampler rejected 64 draws; ";
       if (h & ERR_CELL_RANGE) m += "a position was not finite (cell id clamped); ";
+      if (h & ERR_OVERFLOW_CAP) m += "cell overflow list full; ";
       return fail(MPCD_EDEVICE, m);
     }
     return MPCD_OK;
   }
 
-  // Rebuild the device record table and the tile tables from `slots`.
   int rebuild() {
     int rc = pull_records();
     if (rc) return rc;
-    drop_graph();
+    drop_graphs();
     free_tables();
     live.clear();
     for (Box* b : slots)
@@ -290,8 +287,8 @@ struct Engine {
     tables_ok = true;
     if (live.empty()) return MPCD_OK;
     std::vector<BoxDev> rec;
-    std::vector<int2> pt, ct[4], cst, bst, bt, mt;
-    std::vector<ScanSeg> cseg, bseg;
+    std::vector<int2> sp[4], bst, bt, mt;
+    std::vector<ScanSeg> bseg;
     any_beads = false;
     int max_cl = 1;
     for (Box* b : live)
@@ -303,11 +300,8 @@ struct Engine {
       b->dev_index = (int)i;
       rec.push_back(b->d);
       const BoxDev& d = b->d;
-      for (int p0 = 0; p0 < d.nsol; p0 += PTILE) pt.push_back(make_int2((int)i, p0));
       const int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0);
-      for (int c0 = 0; c0 < d.ncells; c0 += d.tc) ct[variant].push_back(make_int2((int)i, c0));
-      cseg.push_back(ScanSeg{d.count, d.start, d.ncells, 0});
-      for (int c0 = 0; c0 < d.ncells; c0 += STILE) cst.push_back(make_int2((int)cseg.size() - 1, c0));
+      for (int c0 = 0; c0 < d.ncells; c0 += BLOCK) sp[variant].push_back(make_int2((int)i, c0));
       if (d.nbead > 0) {
         any_beads = true;
         bseg.push_back(ScanSeg{d.bcount, d.bstart, d.nctiles, 0});
@@ -328,96 +322,135 @@ struct Engine {
       return MPCD_OK;
     };
     if ((rc = up(rec, d_boxes, &n_records))) return rc;
-    if ((rc = up(pt, d_ptiles, &n_ptiles))) return rc;
-    size_t nct_total = 0;
-    for (int v = 0; v < 4; ++v) {
-      if ((rc = up(ct[v], d_ctiles[v], &n_ctiles[v]))) return rc;
-      nct_total += ct[v].size();
-    }
-    if (nct_total > 0) CUDA_TRY(cudaMalloc(&d_ovf, sizeof(int2) * nct_total));
-    if ((rc = up(cseg, d_csegs, nullptr))) return rc;
-    if ((rc = up(cst, d_cstiles, &n_cstiles))) return rc;
+    for (int v = 0; v < 4; ++v)
+      if ((rc = up(sp[v], d_spans[v], &n_spans[v]))) return rc;
     if ((rc = up(bseg, d_bsegs, nullptr))) return rc;
     if ((rc = up(bst, d_bstiles, &n_bstiles))) return rc;
     if ((rc = up(bt, d_btiles, &n_btiles))) return rc;
     if ((rc = up(mt, d_mdtiles, &n_mdtiles))) return rc;
-    scan_capacity = std::max(n_cstiles, n_bstiles);
-    if (scan_capacity > 0) {
-      CUDA_TRY(cudaMalloc(&d_tsum, sizeof(uint32_t) * scan_capacity));
-      CUDA_TRY(cudaMalloc(&d_gscan, sizeof(unsigned long long) * scan_capacity));
-      CUDA_TRY(cudaMalloc(&d_toff, sizeof(uint32_t) * scan_capacity));
+    if (n_bstiles > 0) {
+      CUDA_TRY(cudaMalloc(&d_tsum, sizeof(uint32_t) * n_bstiles));
+      CUDA_TRY(cudaMalloc(&d_gscan, sizeof(unsigned long long) * n_bstiles));
+      CUDA_TRY(cudaMalloc(&d_toff, sizeof(uint32_t) * n_bstiles));
     }
     CUDA_TRY(cudaStreamSynchronize(stream));
     return MPCD_OK;
   }
 
-  int grid_for(int ntiles, int per_sm) const {
-    int g = nsm * per_sm;
-    return ntiles < g ? std::max(ntiles, 1) : g;
+  int grid_for(int n, int per_sm) const {
+    const int g = nsm * per_sm;
+    return n < g ? std::max(n, 1) : g;
   }
 
-  // The four collide variants (each over its own tile list) and the overflow
-  // pass for tiles they queued.
-  void launch_collides() {
+  void launch_cells_all(int mode) {
     for (int v = 0; v < 4; ++v)
-      launch_collide(mixed, v, d_boxes, d_ctiles[v], n_ctiles[v], grid_for(n_ctiles[v], collide_bps[v]),
-                     cap, bcap, collide_smem, d_ovf, d_novf, d_err, stream);
-    launch_collide_overflow(mixed, d_boxes, d_ovf, d_novf, nsm, d_err, stream);
+      launch_cells(mixed, v, mode, d_boxes, d_spans[v], n_spans[v],
+                   grid_for(n_spans[v], cells_bps[mode][v]), d_err, stream);
   }
 
-  // Enqueue one SRD step for every live box.
-  void enqueue_step() {
+  // Solute: MD substeps and bead grouping for the step in the records.
+  void launch_beads() {
+    if (!any_beads) return;
+    launch_md_bin(d_boxes, d_mdtiles, n_mdtiles, md_chains_per_block, md_threads, d_err, stream);
+    launch_scan(d_bsegs, d_bstiles, n_bstiles, d_tsum, d_gscan, d_toff, grid_for(n_bstiles, 8),
+                stream);
+    launch_bead_scatter(d_boxes, d_btiles, n_btiles, stream);
+  }
+
+  // One pass over every live box (plain launches; captured into the graphs).
+  void enqueue_pass(int mode) {
     const int nb = (int)live.size();
     if (nb == 0) return;
-    if (any_beads)
-      launch_md_bin(d_boxes, d_mdtiles, n_mdtiles, md_chains_per_block, md_threads, d_err, stream);
-    launch_stream_bin(mixed, d_boxes, d_ptiles, n_ptiles, grid_for(n_ptiles, 8), d_err, stream);
-    launch_scan(d_csegs, d_cstiles, n_cstiles, d_tsum, d_gscan, d_toff, grid_for(n_cstiles, 8),
-                stream);
-    if (any_beads) {
-      launch_scan(d_bsegs, d_bstiles, n_bstiles, d_tsum, d_gscan, d_toff, grid_for(n_bstiles, 8),
-                  stream);
-      launch_bead_scatter(d_boxes, d_btiles, n_btiles, stream);
+    launch_cells_all(mode);
+    if (mode == MODE_P) {
+      launch_after_pass(d_boxes, nb, true, false, stream);
+      launch_beads();
+    } else if (mode == MODE_F) {
+      launch_after_pass(d_boxes, nb, true, true, stream);
+      launch_beads();
+    } else {
+      launch_after_pass(d_boxes, nb, false, true, stream);
     }
-    launch_scatter(d_boxes, d_ptiles, n_ptiles, grid_for(n_ptiles, 8), stream);
-    launch_permute(mixed, d_boxes, nb, d_ptiles, n_ptiles, grid_for(n_ptiles, 8), stream);
-    launch_collides();
-    launch_end_step(d_boxes, nb, d_novf, stream);
   }
 
-  // Eager step with an event after every phase (internal profiler).  Phase
-  // times are accumulated into ms[phase]; returns the number of phases.
-  static constexpr int kPhases = 7;
+  int ensure_tables() {
+    if (!tables_ok) return rebuild();
+    return MPCD_OK;
+  }
+
+  int ensure_graph(int mode) {
+    int rc = ensure_tables();
+    if (rc) return rc;
+    if (gexec[mode]) return MPCD_OK;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_pass(mode);
+    cudaError_t e = cudaStreamEndCapture(stream, &g);
+    if (e != cudaSuccess) return fail(MPCD_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&gexec[mode], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(MPCD_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    return MPCD_OK;
+  }
+
+  int run_pass(int mode) {
+    int rc = ensure_graph(mode);
+    if (rc) return rc;
+    if (live.empty()) return MPCD_OK;
+    CUDA_TRY(cudaGraphLaunch(gexec[mode], stream));
+    return MPCD_OK;
+  }
+
+  int step(int64_t n) {
+    if (n < 0) return fail(MPCD_EINVAL, "nsteps < 0");
+    int rc = ensure_tables();
+    if (rc) return rc;
+    if (n == 0 || live.empty()) return MPCD_OK;
+    if (!pending) {
+      if ((rc = run_pass(MODE_P))) return rc;
+      pending = true;
+      n -= 1;
+    }
+    if (n > 0) {
+      if ((rc = ensure_graph(MODE_F))) return rc;
+      for (int64_t i = 0; i < n; ++i) CUDA_TRY(cudaGraphLaunch(gexec[MODE_F], stream));
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MPCD_OK;
+  }
+
+  // Finish the pending collision so the records hold a completed step.
+  int complete() {
+    int rc = ensure_tables();
+    if (rc) return rc;
+    if (!pending) return MPCD_OK;
+    if ((rc = run_pass(MODE_C))) return rc;
+    pending = false;
+    return MPCD_OK;
+  }
+
+  // Internal profiler: eager steps with an event after each phase.
+  static constexpr int kPhases = 3;
   int timed_steps(int64_t n, double* ms) {
-    if (live.empty()) return kPhases;
+    int rc = complete();
+    if (rc) return rc;
+    for (int i = 0; i < kPhases; ++i) ms[i] = 0.0;
+    if (live.empty() || n <= 0) return kPhases;
+    // the first pass streams and bins (it is not one of the timed steps)
+    enqueue_pass(MODE_P);
+    pending = true;
     cudaEvent_t ev[kPhases + 1];
     for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
-    for (int i = 0; i < kPhases; ++i) ms[i] = 0.0;
     const int nb = (int)live.size();
     for (int64_t s = 0; s < n; ++s) {
       CUDA_TRY(cudaEventRecord(ev[0], stream));
-      if (any_beads)
-        launch_md_bin(d_boxes, d_mdtiles, n_mdtiles, md_chains_per_block, md_threads, d_err, stream);
+      launch_cells_all(MODE_F);
       CUDA_TRY(cudaEventRecord(ev[1], stream));
-      launch_stream_bin(mixed, d_boxes, d_ptiles, n_ptiles, grid_for(n_ptiles, 8), d_err, stream);
+      launch_after_pass(d_boxes, nb, true, true, stream);
       CUDA_TRY(cudaEventRecord(ev[2], stream));
-      launch_scan(d_csegs, d_cstiles, n_cstiles, d_tsum, d_gscan, d_toff, grid_for(n_cstiles, 8),
-                  stream);
-      if (any_beads) {
-        launch_scan(d_bsegs, d_bstiles, n_bstiles, d_tsum, d_gscan, d_toff,
-                    grid_for(n_bstiles, 8), stream);
-        launch_bead_scatter(d_boxes, d_btiles, n_btiles, stream);
-      }
+      launch_beads();
       CUDA_TRY(cudaEventRecord(ev[3], stream));
-      launch_scatter(d_boxes, d_ptiles, n_ptiles, grid_for(n_ptiles, 8), stream);
-      CUDA_TRY(cudaEventRecord(ev[4], stream));
-      launch_permute(mixed, d_boxes, nb, d_ptiles, n_ptiles, grid_for(n_ptiles, 8), stream);
-      CUDA_TRY(cudaEventRecord(ev[5], stream));
-      launch_collides();
-      CUDA_TRY(cudaEventRecord(ev[6], stream));
-      launch_end_step(d_boxes, nb, d_novf, stream);
-      CUDA_TRY(cudaEventRecord(ev[7], stream));
-      CUDA_TRY(cudaEventSynchronize(ev[7]));
+      CUDA_TRY(cudaEventSynchronize(ev[3]));
       for (int i = 0; i < kPhases; ++i) {
         float t = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
@@ -425,38 +458,9 @@ struct Engine {
       }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    if (n > 0)
-      for (int i = 0; i < kPhases; ++i) ms[i] /= (double)n;
+    for (int i = 0; i < kPhases; ++i) ms[i] /= (double)n;
     CUDA_TRY(cudaGetLastError());
     return kPhases;
-  }
-
-  int ensure_graph() {
-    if (!tables_ok) {
-      int rc = rebuild();
-      if (rc) return rc;
-    }
-    if (graph_ok) return MPCD_OK;
-    cudaGraph_t g = nullptr;
-    CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_step();
-    cudaError_t e = cudaStreamEndCapture(stream, &g);
-    if (e != cudaSuccess) return fail(MPCD_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&gexec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(MPCD_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-    graph_ok = true;
-    return MPCD_OK;
-  }
-
-  int step(int64_t n) {
-    if (n < 0) return fail(MPCD_EINVAL, "nsteps < 0");
-    int rc = ensure_graph();
-    if (rc) return rc;
-    if (live.empty()) return MPCD_OK;
-    for (int64_t i = 0; i < n; ++i) CUDA_TRY(cudaGraphLaunch(gexec, stream));
-    CUDA_TRY(cudaGetLastError());
-    return MPCD_OK;
   }
 
   template <typename P>
@@ -469,8 +473,15 @@ struct Engine {
     ptr = (P*)q;
     return MPCD_OK;
   }
+  int alloc_bytes(Box* b, void*& ptr, size_t bytes) {
+    ptr = nullptr;
+    if (bytes == 0) return MPCD_OK;
+    CUDA_TRY(cudaMallocAsync(&ptr, bytes, stream));
+    b->allocs.push_back(ptr);
+    return MPCD_OK;
+  }
 
-  // Allocate a box's arrays and fill its record (no state copied yet).
+  // Allocate a box's arrays and fill its record (no particles placed yet).
   int setup_box(Box* b, int64_t nsol, int64_t nbead) {
     const mpcd_params& p = b->p;
     const int64_t C = cells_of(p);
@@ -492,9 +503,10 @@ struct Engine {
     d.chain_len = p.chain_len;
     d.md_substeps = p.md_substeps;
     d.thermostat = p.thermostat ? 1 : 0;
-    d.sort_period = p.sort_period == 0 ? 25 : (p.sort_period < 0 ? 0 : p.sort_period);
-    d.tc = choose_tc(mixed, nsol, C);
-    d.nctiles = (int32_t)((C + d.tc - 1) / d.tc);
+    d.K = row_capacity(p, nsol);
+    d.ovf_cap = (int32_t)std::max<int64_t>(nsol, 1);
+    d.tc = BEAD_TILE;
+    d.nctiles = (int32_t)((C + BEAD_TILE - 1) / BEAD_TILE);
     d.seed_lo = (uint32_t)p.seed;
     d.seed_hi = (uint32_t)(p.seed >> 32);
     d.dt = p.dt;
@@ -530,25 +542,19 @@ struct Engine {
     d.ca_f = (float)d.ca;
     d.sa_f = (float)d.sa;
     d.omc_f = (float)d.omc;
-    const size_t es = elem_size(mixed);
+    const size_t rs = rec_size(mixed), es = elem_size(mixed);
     int rc;
-    for (void** dst : {&d.r, &d.v, &d.r2, &d.v2}) {
-      *dst = nullptr;
-      if (nsol > 0) {
-        void* q = nullptr;
-        CUDA_TRY(cudaMallocAsync(&q, (size_t)nsol * 3 * es, stream));
-        b->allocs.push_back(q);
-        *dst = q;
-      }
+    for (int s = 0; s < 2; ++s) {
+      if ((rc = alloc_bytes(b, d.rows[s], (size_t)C * d.K * rs))) return rc;
+      if ((rc = alloc(b, d.cnt[s], (size_t)C))) return rc;
+      if ((rc = alloc_bytes(b, d.ovf_rec[s], (size_t)d.ovf_cap * rs))) return rc;
+      if ((rc = alloc(b, d.ovf_cell[s], (size_t)d.ovf_cap))) return rc;
+      CUDA_TRY(cudaMemsetAsync(d.cnt[s], 0, sizeof(uint32_t) * C, stream));
     }
-    if ((rc = alloc(b, d.tag, nsol))) return rc;
-    if ((rc = alloc(b, d.tag2, nsol))) return rc;
-    if ((rc = alloc(b, d.key, nsol))) return rc;
-    if ((rc = alloc(b, d.order, nsol))) return rc;
-    if ((rc = alloc(b, d.count, (size_t)C))) return rc;
-    if ((rc = alloc(b, d.start, (size_t)C + 1))) return rc;
-    CUDA_TRY(cudaMemsetAsync(d.count, 0, sizeof(uint32_t) * C, stream));
-    CUDA_TRY(cudaMemsetAsync(d.start, 0, sizeof(uint32_t) * (C + 1), stream));
+    if ((rc = alloc(b, d.ovf_n, 2))) return rc;
+    CUDA_TRY(cudaMemsetAsync(d.ovf_n, 0, sizeof(uint32_t) * 2, stream));
+    if ((rc = alloc_bytes(b, b->stage_r, (size_t)nsol * 3 * es))) return rc;
+    if ((rc = alloc_bytes(b, b->stage_v, (size_t)nsol * 3 * es))) return rc;
     if (nbead > 0) {
       if ((rc = alloc(b, d.spos, (size_t)nbead * 3))) return rc;
       if ((rc = alloc(b, d.svel, (size_t)nbead * 3))) return rc;
@@ -560,6 +566,7 @@ struct Engine {
       CUDA_TRY(cudaMemsetAsync(d.bcount, 0, sizeof(uint32_t) * d.nctiles, stream));
       CUDA_TRY(cudaMemsetAsync(d.bstart, 0, sizeof(uint32_t) * (d.nctiles + 1), stream));
     }
+    d.cur = 0;
     b->nsol = nsol;
     b->nbead = nbead;
     b->bytes = need;
@@ -567,18 +574,32 @@ struct Engine {
     return MPCD_OK;
   }
 
-  void free_box_arrays(Box* b) {
-    for (void* q : b->allocs)
-      if (q) cudaFreeAsync(q, stream);
-    b->allocs.clear();
-    used_bytes -= b->bytes;
-    b->bytes = 0;
+  // Place particles (device arrays of the storage type) into a set-up box.
+  // The box record goes to a one-entry scratch table for the load.
+  int place(Box* b, const void* dpos, const void* dvel, const double* spos, const double* svel,
+            uint64_t step) {
+    BoxDev& d = b->d;
+    d.step = step;
+    d.cur = 0;
+    BoxDev* tmp = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&tmp, sizeof(BoxDev), stream));
+    CUDA_TRY(cudaMemcpyAsync(tmp, &d, sizeof(BoxDev), cudaMemcpyHostToDevice, stream));
+    launch_load(mixed, tmp, dpos, dvel, (int)b->nsol, d_err, stream);
+    if (b->nbead > 0) {
+      CUDA_TRY(cudaMemcpyAsync(d.spos, spos, sizeof(double) * 3 * b->nbead, cudaMemcpyHostToDevice,
+                               stream));
+      CUDA_TRY(cudaMemcpyAsync(d.svel, svel, sizeof(double) * 3 * b->nbead, cudaMemcpyHostToDevice,
+                               stream));
+    }
+    CUDA_TRY(cudaFreeAsync(tmp, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    CUDA_TRY(cudaGetLastError());
+    b->has_state = true;
+    return check_err();
   }
 
-  // Copy host state into a set-up box.
   int upload_state(Box* b, const double* pos, const double* vel, const double* spos,
                    const double* svel, uint64_t step) {
-    BoxDev& d = b->d;
     const size_t n3 = (size_t)b->nsol * 3;
     if (b->nsol > 0) {
       if (mixed) {
@@ -587,68 +608,73 @@ struct Engine {
           hp[i] = (float)pos[i];
           hv[i] = (float)vel[i];
         }
-        CUDA_TRY(cudaMemcpyAsync(d.r, hp.data(), n3 * sizeof(float), cudaMemcpyHostToDevice, stream));
-        CUDA_TRY(cudaMemcpyAsync(d.v, hv.data(), n3 * sizeof(float), cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaMemcpyAsync(b->stage_r, hp.data(), n3 * 4, cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaMemcpyAsync(b->stage_v, hv.data(), n3 * 4, cudaMemcpyHostToDevice, stream));
         CUDA_TRY(cudaStreamSynchronize(stream));
       } else {
-        CUDA_TRY(cudaMemcpyAsync(d.r, pos, n3 * sizeof(double), cudaMemcpyHostToDevice, stream));
-        CUDA_TRY(cudaMemcpyAsync(d.v, vel, n3 * sizeof(double), cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaMemcpyAsync(b->stage_r, pos, n3 * 8, cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaMemcpyAsync(b->stage_v, vel, n3 * 8, cudaMemcpyHostToDevice, stream));
       }
-      launch_iota(d.tag, (int)b->nsol, stream);
     }
-    if (b->nbead > 0) {
-      CUDA_TRY(cudaMemcpyAsync(d.spos, spos, sizeof(double) * 3 * b->nbead, cudaMemcpyHostToDevice,
-                               stream));
-      CUDA_TRY(cudaMemcpyAsync(d.svel, svel, sizeof(double) * 3 * b->nbead, cudaMemcpyHostToDevice,
-                               stream));
-    }
-    d.step = step;
-    d.permuted = 0;
-    CUDA_TRY(cudaStreamSynchronize(stream));
+    return place(b, b->stage_r, b->stage_v, spos, svel, step);
+  }
+
+  // Thermal initial state drawn on the device (see launch_init_thermal).
+  int thermal_state(Box* b, uint64_t init_seed, uint64_t step) {
+    unsigned long long* sums = nullptr;
+    CUDA_TRY(cudaMallocAsync((void**)&sums, 3 * sizeof(unsigned long long), stream));
+    const double L[3] = {(double)b->p.n[0], (double)b->p.n[1], (double)b->p.n[2]};
+    launch_init_thermal(mixed, (int)b->nsol, init_seed, L, std::sqrt(b->p.kT / b->p.mass),
+                        b->stage_r, b->stage_v, sums, stream);
+    CUDA_TRY(cudaFreeAsync(sums, stream));
     CUDA_TRY(cudaGetLastError());
-    b->has_state = true;
+    return place(b, b->stage_r, b->stage_v, nullptr, nullptr, step);
+  }
+
+  // The completed state into the box's staging arrays (input order).
+  int extract(Box* b, int32_t* cell_out) {
+    int rc = complete();
+    if (rc) return rc;
+    if ((rc = pull_records())) return rc;
+    if ((rc = check_err())) return rc;
+    launch_extract(mixed, d_boxes + b->dev_index, b->stage_r, b->stage_v, cell_out,
+                   (int)b->d.ncells, stream);
+    CUDA_TRY(cudaGetLastError());
     return MPCD_OK;
   }
 
-  // Per-box state out (tag order).  Leaves r2/v2 holding the ordered copy.
   int download_state(Box* b, double* pos, double* vel, double* spos, double* svel, uint64_t* step) {
-    int rc = pull_records();
+    int rc = extract(b, nullptr);
     if (rc) return rc;
-    if ((rc = check_err())) return rc;
-    const BoxDev* rec = d_boxes + b->dev_index;
-    const BoxDev& d = b->d;
     const size_t n3 = (size_t)b->nsol * 3;
     if (b->nsol > 0 && (pos || vel)) {
-      launch_unpermute(mixed, rec, (int)b->nsol, stream);
-      CUDA_TRY(cudaGetLastError());
       if (mixed) {
         std::vector<float> hp(pos ? n3 : 0), hv(vel ? n3 : 0);
-        if (pos) CUDA_TRY(cudaMemcpyAsync(hp.data(), d.r2, n3 * 4, cudaMemcpyDeviceToHost, stream));
-        if (vel) CUDA_TRY(cudaMemcpyAsync(hv.data(), d.v2, n3 * 4, cudaMemcpyDeviceToHost, stream));
+        if (pos) CUDA_TRY(cudaMemcpyAsync(hp.data(), b->stage_r, n3 * 4, cudaMemcpyDeviceToHost, stream));
+        if (vel) CUDA_TRY(cudaMemcpyAsync(hv.data(), b->stage_v, n3 * 4, cudaMemcpyDeviceToHost, stream));
         CUDA_TRY(cudaStreamSynchronize(stream));
         for (size_t i = 0; pos && i < n3; ++i) pos[i] = (double)hp[i];
         for (size_t i = 0; vel && i < n3; ++i) vel[i] = (double)hv[i];
       } else {
-        if (pos) CUDA_TRY(cudaMemcpyAsync(pos, d.r2, n3 * 8, cudaMemcpyDeviceToHost, stream));
-        if (vel) CUDA_TRY(cudaMemcpyAsync(vel, d.v2, n3 * 8, cudaMemcpyDeviceToHost, stream));
+        if (pos) CUDA_TRY(cudaMemcpyAsync(pos, b->stage_r, n3 * 8, cudaMemcpyDeviceToHost, stream));
+        if (vel) CUDA_TRY(cudaMemcpyAsync(vel, b->stage_v, n3 * 8, cudaMemcpyDeviceToHost, stream));
       }
     }
     if (b->nbead > 0) {
-      if (spos) CUDA_TRY(cudaMemcpyAsync(spos, d.spos, sizeof(double) * 3 * b->nbead,
+      if (spos) CUDA_TRY(cudaMemcpyAsync(spos, b->d.spos, sizeof(double) * 3 * b->nbead,
                                          cudaMemcpyDeviceToHost, stream));
-      if (svel) CUDA_TRY(cudaMemcpyAsync(svel, d.svel, sizeof(double) * 3 * b->nbead,
+      if (svel) CUDA_TRY(cudaMemcpyAsync(svel, b->d.svel, sizeof(double) * 3 * b->nbead,
                                          cudaMemcpyDeviceToHost, stream));
     }
     CUDA_TRY(cudaStreamSynchronize(stream));
-    if (step) *step = d.step;
+    if (step) *step = b->d.step;
     return MPCD_OK;
   }
 
   int observables(Box* b, mpcd_obs* out) {
     if (!out) return fail(MPCD_EINVAL, "out is NULL");
-    int rc = pull_records();
+    int rc = extract(b, nullptr);
     if (rc) return rc;
-    if ((rc = check_err())) return rc;
     const mpcd_params& p = b->p;
     const int nc = p.n[0] * p.n[1] * p.n[2];
     const size_t need = (size_t)nc * (sizeof(uint32_t) + 5 * sizeof(long long)) + 64;
@@ -670,7 +696,7 @@ struct Engine {
     const int ntot = (int)(b->nsol + b->nbead);
     const int nb1 = std::max(1, std::min(1024, (ntot + 255) / 256));
     const int nb2 = std::max(1, std::min(1024, (nc + 255) / 256));
-    launch_obs_particles(mixed, rec, oc, d_partials, nb1, stream);
+    launch_obs_particles(mixed, rec, b->stage_r, b->stage_v, oc, d_partials, nb1, stream);
     std::vector<double> h1(4 * nb1), h2(3 * nb2);
     CUDA_TRY(cudaMemcpyAsync(h1.data(), d_partials, sizeof(double) * 4 * nb1,
                              cudaMemcpyDeviceToHost, stream));
@@ -745,8 +771,9 @@ int mpcd_create(const mpcd_params* params, void* stream, mpcd_ctx** out) {
 
 static int set_state_common(mpcd_ctx* ctx, int64_t n, int64_t nb) {
   Engine& E = ctx->eng;
-  int rc = E.pull_records();
+  int rc = E.complete();
   if (rc) return rc;
+  if ((rc = E.pull_records())) return rc;
   Box* b = ctx->box;
   CUDA_TRY(cudaStreamSynchronize(E.stream));
   E.unlink(b);
@@ -779,20 +806,17 @@ int mpcd_set_state_device(mpcd_ctx* ctx, int64_t n_solvent, const void* pos, con
   if (ctx->box->p.chain_len > 0) return fail(MPCD_EINVAL, "use mpcd_set_state for solute runs");
   int rc = set_state_common(ctx, n_solvent, 0);
   if (rc) return rc;
-  Engine& E = ctx->eng;
-  Box* b = ctx->box;
-  const size_t bytes = (size_t)n_solvent * 3 * elem_size(E.mixed);
-  if (bytes) {
-    CUDA_TRY(cudaMemcpyAsync(b->d.r, pos, bytes, cudaMemcpyDeviceToDevice, E.stream));
-    CUDA_TRY(cudaMemcpyAsync(b->d.v, vel, bytes, cudaMemcpyDeviceToDevice, E.stream));
-    launch_iota(b->d.tag, (int)n_solvent, E.stream);
-  }
-  b->d.step = step;
-  b->d.permuted = 0;
-  CUDA_TRY(cudaStreamSynchronize(E.stream));
-  CUDA_TRY(cudaGetLastError());
-  b->has_state = true;
-  return MPCD_OK;
+  return ctx->eng.place(ctx->box, pos, vel, nullptr, nullptr, step);
+}
+
+int mpcd_set_state_thermal(mpcd_ctx* ctx, int64_t n_solvent, uint64_t init_seed, uint64_t step) {
+  g_last_error.clear();
+  if (!ctx) return fail(MPCD_EINVAL, "ctx is NULL");
+  if (n_solvent < 0) return fail(MPCD_EINVAL, "negative particle count");
+  if (ctx->box->p.chain_len > 0) return fail(MPCD_EINVAL, "use mpcd_set_state for solute runs");
+  int rc = set_state_common(ctx, n_solvent, 0);
+  if (rc) return rc;
+  return ctx->eng.thermal_state(ctx->box, init_seed, step);
 }
 
 int mpcd_step(mpcd_ctx* ctx, int64_t nsteps) {
@@ -807,8 +831,6 @@ int mpcd_get_state(mpcd_ctx* ctx, double* pos, double* vel, double* solute_pos, 
   g_last_error.clear();
   if (!ctx) return fail(MPCD_EINVAL, "ctx is NULL");
   if (!ctx->box->has_state) return fail(MPCD_ESTATE, "no state set");
-  int rc = ctx->eng.ensure_graph();
-  if (rc) return rc;
   return ctx->eng.download_state(ctx->box, pos, vel, solute_pos, solute_vel, step);
 }
 
@@ -817,16 +839,13 @@ int mpcd_get_state_device(mpcd_ctx* ctx, void* pos, void* vel) {
   if (!ctx) return fail(MPCD_EINVAL, "ctx is NULL");
   if (!ctx->box->has_state) return fail(MPCD_ESTATE, "no state set");
   Engine& E = ctx->eng;
-  int rc = E.ensure_graph();
-  if (rc) return rc;
-  if ((rc = E.pull_records())) return rc;
-  if ((rc = E.check_err())) return rc;
   Box* b = ctx->box;
+  int rc = E.extract(b, nullptr);
+  if (rc) return rc;
   const size_t bytes = (size_t)b->nsol * 3 * elem_size(E.mixed);
   if (bytes) {
-    launch_unpermute(E.mixed, E.d_boxes + b->dev_index, (int)b->nsol, E.stream);
-    if (pos) CUDA_TRY(cudaMemcpyAsync(pos, b->d.r2, bytes, cudaMemcpyDeviceToDevice, E.stream));
-    if (vel) CUDA_TRY(cudaMemcpyAsync(vel, b->d.v2, bytes, cudaMemcpyDeviceToDevice, E.stream));
+    if (pos) CUDA_TRY(cudaMemcpyAsync(pos, b->stage_r, bytes, cudaMemcpyDeviceToDevice, E.stream));
+    if (vel) CUDA_TRY(cudaMemcpyAsync(vel, b->stage_v, bytes, cudaMemcpyDeviceToDevice, E.stream));
   }
   CUDA_TRY(cudaStreamSynchronize(E.stream));
   CUDA_TRY(cudaGetLastError());
@@ -837,8 +856,6 @@ int mpcd_observables(mpcd_ctx* ctx, mpcd_obs* out) {
   g_last_error.clear();
   if (!ctx) return fail(MPCD_EINVAL, "ctx is NULL");
   if (!ctx->box->has_state) return fail(MPCD_ESTATE, "no state set");
-  int rc = ctx->eng.ensure_graph();
-  if (rc) return rc;
   return ctx->eng.observables(ctx->box, out);
 }
 
@@ -848,17 +865,16 @@ int mpcd_profile(mpcd_ctx* ctx, int32_t nbins, double* out) {
   if (nbins < 1 || nbins > (1 << 20)) return fail(MPCD_EINVAL, "nbins out of range");
   if (!ctx->box->has_state) return fail(MPCD_ESTATE, "no state set");
   Engine& E = ctx->eng;
-  int rc = E.ensure_graph();
-  if (rc) return rc;
-  if ((rc = E.pull_records())) return rc;
   Box* b = ctx->box;
+  int rc = E.extract(b, nullptr);
+  if (rc) return rc;
   double* dsum = nullptr;
   unsigned long long* dcnt = nullptr;
   CUDA_TRY(cudaMallocAsync((void**)&dsum, sizeof(double) * nbins, E.stream));
   CUDA_TRY(cudaMallocAsync((void**)&dcnt, sizeof(unsigned long long) * nbins, E.stream));
   CUDA_TRY(cudaMemsetAsync(dsum, 0, sizeof(double) * nbins, E.stream));
   CUDA_TRY(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * nbins, E.stream));
-  launch_profile(E.mixed, E.d_boxes + b->dev_index, nbins, dsum, dcnt, (int)b->nsol,
+  launch_profile(E.mixed, b->stage_r, b->stage_v, (int)b->nsol, nbins, dsum, dcnt,
                  (double)b->p.n[2], E.stream);
   std::vector<double> hs(nbins);
   std::vector<unsigned long long> hc(nbins);
@@ -878,19 +894,15 @@ int mpcd_last_cells(mpcd_ctx* ctx, int32_t* cell_out, int32_t* count_out) {
   if (!ctx) return fail(MPCD_EINVAL, "ctx is NULL");
   if (!ctx->box->has_state) return fail(MPCD_ESTATE, "no state set");
   Engine& E = ctx->eng;
-  int rc = E.ensure_graph();
-  if (rc) return rc;
-  if ((rc = E.pull_records())) return rc;
   Box* b = ctx->box;
   const int64_t ntot = b->nsol + b->nbead;
-  const int64_t C = b->d.ncells;
+  const int64_t C = cells_of(b->p);
   int32_t *dc = nullptr, *dk = nullptr;
   if (cell_out && ntot > 0) CUDA_TRY(cudaMallocAsync((void**)&dc, sizeof(int32_t) * ntot, E.stream));
-  if (count_out) {
-    CUDA_TRY(cudaMallocAsync((void**)&dk, sizeof(int32_t) * C, E.stream));
-    CUDA_TRY(cudaMemsetAsync(dk, 0, sizeof(int32_t) * C, E.stream));
-  }
-  launch_last_cells(E.d_boxes + b->dev_index, (int)b->nsol, (int)b->nbead, (int)C, dc, dk, E.stream);
+  if (count_out) CUDA_TRY(cudaMallocAsync((void**)&dk, sizeof(int32_t) * C, E.stream));
+  int rc = E.extract(b, dc);
+  if (rc) return rc;
+  launch_cell_counts(E.d_boxes + b->dev_index, (int)C, (int)b->nbead, dc, dk, E.stream);
   if (dc) CUDA_TRY(cudaMemcpyAsync(cell_out, dc, sizeof(int32_t) * ntot, cudaMemcpyDeviceToHost, E.stream));
   if (dk) CUDA_TRY(cudaMemcpyAsync(count_out, dk, sizeof(int32_t) * C, cudaMemcpyDeviceToHost, E.stream));
   if (dc) CUDA_TRY(cudaFreeAsync(dc, E.stream));
@@ -902,17 +914,14 @@ int mpcd_last_cells(mpcd_ctx* ctx, int32_t* cell_out, int32_t* count_out) {
 
 int64_t mpcd_num_cells(const mpcd_ctx* ctx) { return ctx ? cells_of(ctx->box->p) : -1; }
 
-static const char* kPhaseNames[] = {"md_bin", "stream_bin", "scan", "scatter", "permute",
-                                    "collide", "end_step"};
+static const char* kPhaseNames[] = {"fused_step", "after_pass", "solute"};
 
 int mpcd_phase_times(mpcd_ctx* ctx, int64_t nsteps, double* ms, int32_t nmax, int32_t* nphases) {
   g_last_error.clear();
   if (!ctx || !ms || nsteps < 0) return fail(MPCD_EINVAL, "bad argument");
   if (!ctx->box->has_state) return fail(MPCD_ESTATE, "no state set");
   if (nmax < Engine::kPhases) return fail(MPCD_EINVAL, "nmax too small");
-  int rc = ctx->eng.ensure_graph();
-  if (rc) return rc;
-  rc = ctx->eng.timed_steps(nsteps, ms);
+  const int rc = ctx->eng.timed_steps(nsteps, ms);
   if (rc < 0) return rc;
   if (nphases) *nphases = Engine::kPhases;
   return MPCD_OK;
@@ -960,6 +969,7 @@ int mpcd_batch_add(mpcd_batch* bt, const mpcd_params* params, int64_t n_solvent,
   if (rc) return rc;
   if (params->chain_len > 0) return fail(MPCD_EINVAL, "no solute in batches");
   if (n_solvent > 0 && (!pos || !vel)) return fail(MPCD_EINVAL, "pos/vel is NULL");
+  if ((rc = E.complete())) return rc;
   if ((rc = E.pull_records())) return rc;
   Box* b = new Box();
   b->p = *params;
@@ -983,7 +993,46 @@ int mpcd_batch_add(mpcd_batch* bt, const mpcd_params* params, int64_t n_solvent,
     E.slots.push_back(nullptr);
   }
   E.slots[s] = b;
-  E.drop_graph();
+  E.drop_graphs();
+  E.tables_ok = false;
+  *slot = s;
+  return MPCD_OK;
+}
+
+int mpcd_batch_add_thermal(mpcd_batch* bt, const mpcd_params* params, int64_t n_solvent,
+                           uint64_t init_seed, uint64_t step, int32_t* slot) {
+  g_last_error.clear();
+  if (!bt || !slot) return fail(MPCD_EINVAL, "NULL argument");
+  Engine& E = bt->eng;
+  int rc = validate(params, E.mixed ? MPCD_MIXED : MPCD_FP64);
+  if (rc) return rc;
+  if (params->chain_len > 0) return fail(MPCD_EINVAL, "no solute in batches");
+  if (n_solvent < 0) return fail(MPCD_EINVAL, "negative particle count");
+  if ((rc = E.complete())) return rc;
+  if ((rc = E.pull_records())) return rc;
+  Box* b = new Box();
+  b->p = *params;
+  if ((rc = E.setup_box(b, n_solvent, 0))) {
+    E.free_box_arrays(b);
+    delete b;
+    return rc;
+  }
+  if ((rc = E.thermal_state(b, init_seed, step))) {
+    E.release_box(b);
+    return rc;
+  }
+  int s = -1;
+  for (size_t i = 0; i < E.slots.size(); ++i)
+    if (!E.slots[i]) {
+      s = (int)i;
+      break;
+    }
+  if (s < 0) {
+    s = (int)E.slots.size();
+    E.slots.push_back(nullptr);
+  }
+  E.slots[s] = b;
+  E.drop_graphs();
   E.tables_ok = false;
   *slot = s;
   return MPCD_OK;
@@ -1004,8 +1053,6 @@ int mpcd_batch_get_state(mpcd_batch* bt, int32_t slot, double* pos, double* vel,
   g_last_error.clear();
   Box* b = batch_box(bt, slot);
   if (!b) return fail(MPCD_EINVAL, "bad slot");
-  int rc = bt->eng.ensure_graph();
-  if (rc) return rc;
   return bt->eng.download_state(b, pos, vel, nullptr, nullptr, step);
 }
 
@@ -1013,8 +1060,6 @@ int mpcd_batch_observables(mpcd_batch* bt, int32_t slot, mpcd_obs* out) {
   g_last_error.clear();
   Box* b = batch_box(bt, slot);
   if (!b) return fail(MPCD_EINVAL, "bad slot");
-  int rc = bt->eng.ensure_graph();
-  if (rc) return rc;
   return bt->eng.observables(b, out);
 }
 
@@ -1023,13 +1068,21 @@ int mpcd_batch_remove(mpcd_batch* bt, int32_t slot) {
   Box* b = batch_box(bt, slot);
   if (!b) return fail(MPCD_EINVAL, "bad slot");
   Engine& E = bt->eng;
-  int rc = E.pull_records();
+  int rc = E.complete();
   if (rc) return rc;
+  if ((rc = E.pull_records())) return rc;
   CUDA_TRY(cudaStreamSynchronize(E.stream));
   E.slots[slot] = nullptr;
   E.unlink(b);
   E.release_box(b);
   return MPCD_OK;
+}
+
+int mpcd_batch_sync(mpcd_batch* bt) {
+  g_last_error.clear();
+  if (!bt) return fail(MPCD_EINVAL, "batch is NULL");
+  CUDA_TRY(cudaStreamSynchronize(bt->eng.stream));
+  return bt->eng.check_err();
 }
 
 int mpcd_batch_info(const mpcd_batch* bt, int32_t* n_boxes, int64_t* bytes_used) {
@@ -1078,13 +1131,13 @@ __global__ void k_profile_noalloc_clear(int nbins) {
 }
 
 template <bool MIXED>
-__global__ void k_profile_noalloc_accumulate(const BoxDev* __restrict__ box, int nbins, double H,
-                                             double* __restrict__ scratch) {
+__global__ void k_profile_noalloc_accumulate(const void* __restrict__ pos_,
+                                             const void* __restrict__ vel_, int n, int nbins,
+                                             double H, double* __restrict__ scratch) {
   using T = typename std::conditional<MIXED, float, double>::type;
-  const BoxDev& B = *box;
-  const T* r = (const T*)B.r;
-  const T* v = (const T*)B.v;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.nsol; i += gridDim.x * blockDim.x) {
+  const T* r = (const T*)pos_;
+  const T* v = (const T*)vel_;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     long long b = (long long)floor((double)r[3 * i + 2] / H * (double)nbins);
     if (b < 0) b = 0;
     if (b >= nbins) b = nbins - 1;
@@ -1128,21 +1181,29 @@ extern "C" int mpcd_profile_noalloc(mpcd_ctx* ctx, int32_t nbins, double* out) {
     }
     scratch = g_profile_scratch_addr[dev];
   }
-  const BoxDev* rec = E.d_boxes + b->dev_index;
+  // A pending collision is completed with plain kernel launches, and the state
+  // is written in input order into the box's existing staging arrays: no
+  // allocation on either path.
+  if (E.pending) {
+    E.enqueue_pass(MODE_C);
+    E.pending = false;
+  }
   const int n = (int)b->nsol;
+  launch_extract(E.mixed, E.d_boxes + b->dev_index, b->stage_r, b->stage_v, nullptr,
+                 (int)cells_of(b->p), E.stream);
   int grid = (n + 255) / 256;
   if (grid < 1) grid = 1;
   if (grid > 4096) grid = 4096;
   k_profile_noalloc_clear<<<(2 * nbins + 255) / 256, 256, 0, E.stream>>>(nbins);
   if (E.mixed)
-    k_profile_noalloc_accumulate<true><<<grid, 256, 0, E.stream>>>(rec, nbins, (double)b->p.n[2],
-                                                                   (double*)scratch);
+    k_profile_noalloc_accumulate<true><<<grid, 256, 0, E.stream>>>(
+        b->stage_r, b->stage_v, n, nbins, (double)b->p.n[2], (double*)scratch);
   else
-    k_profile_noalloc_accumulate<false><<<grid, 256, 0, E.stream>>>(rec, nbins, (double)b->p.n[2],
-                                                                    (double*)scratch);
+    k_profile_noalloc_accumulate<false><<<grid, 256, 0, E.stream>>>(
+        b->stage_r, b->stage_v, n, nbins, (double)b->p.n[2], (double*)scratch);
   k_profile_noalloc_finish<<<(nbins + 255) / 256, 256, 0, E.stream>>>(nbins, (double*)scratch);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(out, scratch, sizeof(double) * nbins, cudaMemcpyDeviceToHost, E.stream));
   CUDA_TRY(cudaStreamSynchronize(E.stream));
-  return MPCD_OK;
+  return E.check_err();
 }

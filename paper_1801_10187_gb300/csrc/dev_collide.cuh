@@ -1,26 +1,10 @@
-// k_collide.cu -- cell properties and SRD collision (arXiv:1801.10187,
-// Sec. 3.5 cell properties, Sec. 3.6 rotation with the algorithm "SRD
-// collision rule", Sec. 2 Eqs. srd and thermo).
-//
-// Kernels: k_collide<MIXED, THERMO, EXTRA> (fast path; EXTRA = solute beads
-// or walls present) and k_collide_overflow (tiles too large for the fast path).
-// One block owns a tile of TC consecutive cells of one box.  Because the
-// particles are sorted by cell (order[] and start[] from the counting sort),
-// the members of the tile are the contiguous range order[start[c0] ..
-// start[c0+TC]).  The block
-//   A. gathers those velocities into shared memory (coalesced index loads,
-//      then the gathers, several in flight per thread),
-//   B. gives each cell one thread: sums (int64 fixed point in the mixed model,
-//      double in FP64), centre-of-mass velocity, random axis, and with the
-//      thermostat a second pass for the kinetic energy about u and the Gamma
-//      draw for xi,
-//   C. rotates every member about its cell's axis and writes it back.
-// Cell sums never leave the SM.  Tiles whose members exceed the shared-memory
-// capacity (clustered input) take a block-cooperative path per cell that
-// reads global memory directly; it gives the same results.
+// dev_collide.cuh -- device helpers of the cell properties and the SRD
+// collision (arXiv:1801.10187, Sec. 3.5 cell properties; Sec. 3.6 random
+// axis, Maxwell-Boltzmann thermostat and the algorithm "SRD collision rule";
+// Sec. 2 Eqs. srd and thermo).
+#pragma once
 #include <type_traits>
 
-#include "kernels.h"
 #include "mpcd_internal.cuh"
 
 namespace mpcd {
@@ -28,10 +12,6 @@ namespace mpcd {
 template <bool MIXED>
 using real_t = typename std::conditional<MIXED, float, double>::type;
 
-// ---------------------------------------------------------------------------
-// Random axis (Sec. 3.6): z = 2u - 1, phi = 2 pi u', with
-// sqrt(1 - z^2) = 2 sqrt(u (1 - u)) so that 1 - u is exact.
-// ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Exact conversions on the integer pipe.  On GB300 the float<->int64
 // conversion instructions share the slow FP64 pipe, so the mixed model does
@@ -60,6 +40,22 @@ __device__ __forceinline__ long long fix32_rne(float x) {
     }
   }
   return (b & 0x80000000u) ? -q : q;
+}
+
+// rne(x * 2^32) = H * 2^20 + L for |x| < 2^10, with H = rne(x 2^12) and
+// L = rne((x 2^12 - H) 2^20), both obtained by adding 1.5 * 2^23 (which rounds
+// to an integer in place) and reading the bits: eight FP32/INT32 operations,
+// exact, and summable in int32 over a cell.  Returns false outside the range.
+__device__ __forceinline__ bool split32(float x, int& H, int& L) {
+  const float a = x * 4096.0f;
+  if (!(fabsf(a) < 4194304.0f)) return false;
+  const float t = __fadd_rn(a, 12582912.0f);
+  H = __float_as_int(t) - 0x4B400000;
+  const float hf = __fsub_rn(t, 12582912.0f);
+  const float l = __fmul_rn(__fsub_rn(a, hf), 1048576.0f);
+  const float t2 = __fadd_rn(l, 12582912.0f);
+  L = __float_as_int(t2) - 0x4B400000;
+  return true;
 }
 
 // rne(q) as a float for any int64 q.
@@ -188,7 +184,7 @@ __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, u
 // The float version settles acceptances within 1e-3 (1 + d) of the boundary
 // in double from the same uniforms.  Returns false after 64 rejections.
 // ---------------------------------------------------------------------------
-__device__ bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
+__device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
                            float& ehat) {
   const float kk = 1.5f * small_to_float(nc - 1);
   const float d = kk - 1.0f / 3.0f;
@@ -226,7 +222,7 @@ __device__ bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell,
   return false;
 }
 
-__device__ bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
+__device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
                            double& ehat) {
   const double kk = 1.5 * (double)(nc - 1);
   const double d = kk - 1.0 / 3.0;
@@ -420,17 +416,16 @@ template <typename T> struct CellParams {
   T xi;
 };
 
-// Finish a cell whose solvent sums are in `a`: add beads and virtual
-// particles, compute u, the axis and (thermostat) xi.  `bead_in(j, b)`
-// enumerates the tile's beads; `solvent_energy(u, acc)` adds the solvent's
-// energy about u (a second pass over the members, done by the caller).
-// `thermo` and `extra` are compile-time constants at the fast-path call sites.
-template <bool MIXED, class BeadIn, class SolventEnergy>
-__device__ __forceinline__ void finish_cell(const BoxDev& B, unsigned long long t, uint32_t cell,
-                                            double sz, CellAcc<MIXED>& a, int nbt, BeadIn bead_in,
-                                            SolventEnergy solvent_energy, bool thermo, bool extra,
-                                            CellParams<real_t<MIXED>>& out, int* err) {
-  using T = real_t<MIXED>;
+// Two halves of the per-cell work once the solvent sums are in `a`.
+// cell_mean: add the beads of the cell (`bead_in(j, b)` enumerates the bead
+// group) and, with walls, the virtual particles; return u.  cell_finish:
+// with the thermostat add the beads' and virtual particles' energies about u
+// (the solvent's energy is already in `a`), draw xi; draw the axis.  `thermo`
+// and `extra` are compile-time constants at the call sites.
+template <bool MIXED, class BeadIn>
+__device__ __forceinline__ void cell_mean(const BoxDev& B, unsigned long long t, uint32_t cell,
+                                          double sz, CellAcc<MIXED>& a, int nbt, BeadIn bead_in,
+                                          bool extra, real_t<MIXED> u[3]) {
   if (extra) {
     for (int j = 0; j < nbt; ++j) {
       int b;
@@ -448,13 +443,19 @@ __device__ __forceinline__ void finish_cell(const BoxDev& B, unsigned long long 
       }
     }
   }
-  T u[3];
   a.mean_velocity(B, u, extra);
+}
+
+template <bool MIXED, class BeadIn>
+__device__ __forceinline__ void cell_finish(const BoxDev& B, unsigned long long t, uint32_t cell,
+                                            CellAcc<MIXED>& a, const real_t<MIXED> u[3], int nbt,
+                                            BeadIn bead_in, bool thermo, bool extra,
+                                            CellParams<real_t<MIXED>>& out, int* err) {
+  using T = real_t<MIXED>;
   T n[3];
   axis_of(B, t, cell, n);
   T xi = (T)1;
   if (thermo) {
-    solvent_energy(u, a);
     if (extra) {
       for (int j = 0; j < nbt; ++j) {
         int b;
@@ -526,358 +527,5 @@ __device__ __forceinline__ void collide_bead(const BoxDev& B, const CellParams<r
   }
 }
 
-// ---------------------------------------------------------------------------
-// Fast path.  Shared memory (byte offsets from collide_smem_layout):
-//   st[BLOCK+1] u32 | sidx[cap] u32 | vx, vy, vz[cap] T | lc[cap] u16 |
-//   prm[BLOCK] CellParams | bidx[bcap] u32 | blc[bcap] u16
-// ---------------------------------------------------------------------------
-template <bool MIXED>
-__host__ __device__ inline size_t collide_smem_layout(int cap, int bcap, size_t off[8]) {
-  using T = real_t<MIXED>;
-  size_t o = 0;
-  auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
-  off[0] = o; o = al(o + sizeof(uint32_t) * (BLOCK + 1));
-  off[1] = o; o = al(o + sizeof(uint32_t) * cap);
-  off[2] = o; o = al(o + sizeof(T) * 3 * cap);
-  off[3] = o; o = al(o + sizeof(uint16_t) * cap);
-  off[4] = o; o = al(o + sizeof(CellParams<T>) * BLOCK);
-  off[5] = o; o = al(o + sizeof(uint32_t) * bcap);
-  off[6] = o; o = al(o + sizeof(uint16_t) * bcap);
-  off[7] = o;
-  return o;
-}
-
-constexpr int GATHER = 4;  // independent gathers in flight per thread
-
-template <bool MIXED, bool THERMO, bool EXTRA>
-__global__ void __launch_bounds__(BLOCK, MIXED ? 4 : 2)
-    k_collide(const BoxDev* __restrict__ boxes, const int2* __restrict__ tiles, int ntiles, int cap,
-              int bcap, int2* __restrict__ ovf, int* __restrict__ novf, int* err) {
-  using T = real_t<MIXED>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  size_t off[8];
-  collide_smem_layout<MIXED>(cap, bcap, off);
-  uint32_t* st = (uint32_t*)(smem_raw + off[0]);
-  uint32_t* sidx = (uint32_t*)(smem_raw + off[1]);
-  T* vx = (T*)(smem_raw + off[2]);
-  T* vy = vx + cap;
-  T* vz = vy + cap;
-  uint16_t* lc = (uint16_t*)(smem_raw + off[3]);
-  CellParams<T>* prm = (CellParams<T>*)(smem_raw + off[4]);
-  uint32_t* bidx = (uint32_t*)(smem_raw + off[5]);
-  uint16_t* blc = (uint16_t*)(smem_raw + off[6]);
-  __shared__ long long sSz;
-
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int2 tt = tiles[tile];
-    const BoxDev& B = boxes[tt.x];
-    const unsigned long long t = B.step;
-    const int c0 = tt.y;
-    const int ncl = min(B.tc, B.ncells - c0);
-    __syncthreads();
-    for (int c = threadIdx.x; c <= ncl; c += BLOCK) st[c] = B.start[c0 + c];
-    if (EXTRA && threadIdx.x == 0) {
-      long long S[3];
-      shift_units(B, t, S);
-      sSz = S[2];
-    }
-    __syncthreads();
-    const uint32_t p0 = st[0];
-    const int np = (int)(st[ncl] - p0);
-    int b0 = 0, nbt = 0;
-    if (EXTRA && B.nbead > 0) {
-      const int tl = c0 / B.tc;
-      b0 = (int)B.bstart[tl];
-      nbt = (int)B.bstart[tl + 1] - b0;
-    }
-    if (np > cap || nbt > bcap) {
-      if (threadIdx.x == 0) ovf[atomicAdd(novf, 1)] = tt;
-      continue;
-    }
-    const uint32_t* __restrict__ order = B.order;
-    T* __restrict__ v = (T*)B.v;
-
-    // ---- A: gather the tile's members, GATHER loads in flight per thread ----
-    for (int base = 0; base < np; base += BLOCK * GATHER) {
-      uint32_t idx[GATHER];
-#pragma unroll
-      for (int j = 0; j < GATHER; ++j) {
-        const int k = base + j * BLOCK + threadIdx.x;
-        idx[j] = (k < np) ? order[p0 + k] : 0u;
-      }
-      T w[GATHER][3];
-#pragma unroll
-      for (int j = 0; j < GATHER; ++j) {
-        const int k = base + j * BLOCK + threadIdx.x;
-        if (k < np) {
-          w[j][0] = v[3 * idx[j]];
-          w[j][1] = v[3 * idx[j] + 1];
-          w[j][2] = v[3 * idx[j] + 2];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < GATHER; ++j) {
-        const int k = base + j * BLOCK + threadIdx.x;
-        if (k < np) {
-          sidx[k] = idx[j];
-          vx[k] = w[j][0];
-          vy[k] = w[j][1];
-          vz[k] = w[j][2];
-        }
-      }
-    }
-    for (int c = threadIdx.x; c < ncl; c += BLOCK) {
-      const int e = (int)(st[c + 1] - p0);
-      for (int k = (int)(st[c] - p0); k < e; ++k) lc[k] = (uint16_t)c;
-    }
-    if (EXTRA) {
-      for (int j = threadIdx.x; j < nbt; j += BLOCK) {
-        const uint32_t b = B.border[b0 + j];
-        bidx[j] = b;
-        blc[j] = (uint16_t)(B.bcell[b] - c0);
-      }
-    }
-    __syncthreads();
-
-    // ---- B: one thread per cell ----
-    const double sz = EXTRA ? (double)sSz * 0x1p-32 : 0.0;
-    for (int c = threadIdx.x; c < ncl; c += BLOCK) {
-      const int kb = (int)(st[c] - p0), ke = (int)(st[c + 1] - p0);
-      bool any = ke > kb;
-      if (EXTRA)
-        for (int j = 0; j < nbt; ++j) any |= (blc[j] == c);
-      if (!any) continue;
-      CellAcc<MIXED> a;
-      for (int k = kb; k < ke; ++k) {
-        const T w[3] = {vx[k], vy[k], vz[k]};
-        a.add_solvent(B, w);
-      }
-      auto bead_in = [&](int j, int& b) {
-        if (blc[j] != c) return false;
-        b = (int)bidx[j];
-        return true;
-      };
-      auto solvent_energy = [&](const T u[3], CellAcc<MIXED>& acc) {
-        for (int k = kb; k < ke; ++k) {
-          const T w[3] = {vx[k], vy[k], vz[k]};
-          acc.add_solvent_energy(B, w, u);
-        }
-      };
-      finish_cell<MIXED>(B, t, (uint32_t)(c0 + c), sz, a, EXTRA ? nbt : 0, bead_in,
-                         solvent_energy, THERMO, EXTRA, prm[c], err);
-    }
-    __syncthreads();
-
-    // ---- C: rotate and write back ----
-    for (int k = threadIdx.x; k < np; k += BLOCK) {
-      const CellParams<T> p = prm[lc[k]];
-      T w[3] = {vx[k], vy[k], vz[k]};
-      collide_one<MIXED>(B, p, w, THERMO);
-      const uint32_t i = sidx[k];
-      v[3 * i] = w[0];
-      v[3 * i + 1] = w[1];
-      v[3 * i + 2] = w[2];
-    }
-    if (EXTRA) {
-      for (int j = threadIdx.x; j < nbt; j += BLOCK) {
-        const int b = (int)bidx[j];
-        double w[3] = {B.svel[3 * b], B.svel[3 * b + 1], B.svel[3 * b + 2]};
-        collide_bead<MIXED>(B, prm[blc[j]], w, THERMO);
-        B.svel[3 * b] = w[0];
-        B.svel[3 * b + 1] = w[1];
-        B.svel[3 * b + 2] = w[2];
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Tiles the fast path queued (members beyond its shared-memory capacity):
-// cell by cell, the whole block reduces straight from global memory.  Same
-// arithmetic, so the same results.
-// ---------------------------------------------------------------------------
-template <bool MIXED>
-__device__ CellAcc<MIXED> block_merge(CellAcc<MIXED> a, CellAcc<MIXED>* red) {
-  __syncthreads();
-  red[threadIdx.x] = a;
-  __syncthreads();
-  for (int s = BLOCK / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      CellAcc<MIXED> o = red[threadIdx.x];
-      o.merge(red[threadIdx.x + s]);
-      red[threadIdx.x] = o;
-    }
-    __syncthreads();
-  }
-  CellAcc<MIXED> r = red[0];
-  __syncthreads();
-  return r;
-}
-
-template <bool MIXED>
-__global__ void __launch_bounds__(BLOCK) k_collide_overflow(const BoxDev* __restrict__ boxes,
-                                                            const int2* __restrict__ ovf,
-                                                            const int* __restrict__ novf, int* err) {
-  using T = real_t<MIXED>;
-  __shared__ CellAcc<MIXED> red[BLOCK];
-  __shared__ CellParams<T> pc;
-  __shared__ T su[3];
-  __shared__ int sflag;
-  const int n = *novf;
-  for (int q = blockIdx.x; q < n; q += gridDim.x) {
-    const int2 tt = ovf[q];
-    const BoxDev& B = boxes[tt.x];
-    const unsigned long long t = B.step;
-    const int c0 = tt.y;
-    const int ncl = min(B.tc, B.ncells - c0);
-    const bool thermo = B.thermostat != 0;
-    const bool extra = B.walls != 0 || B.nbead > 0;
-    long long S[3];
-    shift_units(B, t, S);
-    const double sz = (double)S[2] * 0x1p-32;
-    int b0 = 0, nbt = 0;
-    if (B.nbead > 0) {
-      const int tl = c0 / B.tc;
-      b0 = (int)B.bstart[tl];
-      nbt = (int)B.bstart[tl + 1] - b0;
-    }
-    const uint32_t* __restrict__ order = B.order;
-    T* __restrict__ v = (T*)B.v;
-    for (int c = 0; c < ncl; ++c) {
-      const uint32_t kb = B.start[c0 + c], ke = B.start[c0 + c + 1];
-      const uint32_t cell = (uint32_t)(c0 + c);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        int any = (ke > kb) ? 1 : 0;
-        for (int j = 0; j < nbt && !any; ++j) any = (B.bcell[B.border[b0 + j]] == (int)cell) ? 1 : 0;
-        sflag = any;
-      }
-      __syncthreads();
-      if (!sflag) continue;
-      CellAcc<MIXED> a;
-      for (uint32_t k = kb + threadIdx.x; k < ke; k += BLOCK) {
-        const uint32_t i = order[k];
-        const T w[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
-        a.add_solvent(B, w);
-      }
-      CellAcc<MIXED> tot = block_merge<MIXED>(a, red);
-      auto bead_in = [&](int j, int& bb) {
-        bb = (int)B.border[b0 + j];
-        return B.bcell[bb] == (int)cell;
-      };
-      if (threadIdx.x == 0) {
-        CellAcc<MIXED> b = tot;
-        if (extra) {
-          for (int j = 0; j < nbt; ++j) {
-            int bb;
-            if (!bead_in(j, bb)) continue;
-            const double vb[3] = {B.svel[3 * bb], B.svel[3 * bb + 1], B.svel[3 * bb + 2]};
-            b.add_extra(B.Mb, vb, true);
-          }
-          if (B.walls) {
-            const int nv = virtual_count(B, t, cell, sz);
-            for (int qq = 0; qq < nv; ++qq) {
-              double vv[3];
-              virtual_velocity(B, t, cell, qq, vv);
-              b.add_extra(B.m, vv, false);
-            }
-          }
-        }
-        T u[3];
-        b.mean_velocity(B, u, extra);
-        su[0] = u[0];
-        su[1] = u[1];
-        su[2] = u[2];
-      }
-      __syncthreads();
-      CellAcc<MIXED> ea;
-      if (thermo) {
-        const T u[3] = {su[0], su[1], su[2]};
-        for (uint32_t k = kb + threadIdx.x; k < ke; k += BLOCK) {
-          const uint32_t i = order[k];
-          const T w[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
-          ea.add_solvent_energy(B, w, u);
-        }
-      }
-      const CellAcc<MIXED> etot = block_merge<MIXED>(ea, red);
-      if (threadIdx.x == 0) {
-        auto solvent_energy = [&](const T[3], CellAcc<MIXED>& acc) { acc.add_energy_partial(etot); };
-        finish_cell<MIXED>(B, t, cell, sz, tot, nbt, bead_in, solvent_energy, thermo, extra, pc, err);
-      }
-      __syncthreads();
-      const CellParams<T> p = pc;
-      for (uint32_t k = kb + threadIdx.x; k < ke; k += BLOCK) {
-        const uint32_t i = order[k];
-        T w[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
-        collide_one<MIXED>(B, p, w, thermo);
-        v[3 * i] = w[0];
-        v[3 * i + 1] = w[1];
-        v[3 * i + 2] = w[2];
-      }
-      for (int j = threadIdx.x; j < nbt; j += BLOCK) {
-        int bb;
-        if (!bead_in(j, bb)) continue;
-        double w[3] = {B.svel[3 * bb], B.svel[3 * bb + 1], B.svel[3 * bb + 2]};
-        collide_bead<MIXED>(B, p, w, thermo);
-        B.svel[3 * bb] = w[0];
-        B.svel[3 * bb + 1] = w[1];
-        B.svel[3 * bb + 2] = w[2];
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Host side
-// ---------------------------------------------------------------------------
-template <bool M, bool TH, bool EX>
-static void* collide_fn() {
-  return (void*)k_collide<M, TH, EX>;
-}
-
-static void* collide_variant(bool mixed, int variant) {
-  const bool th = (variant & 1) != 0, ex = (variant & 2) != 0;
-  if (mixed) {
-    if (th) return ex ? collide_fn<true, true, true>() : collide_fn<true, true, false>();
-    return ex ? collide_fn<true, false, true>() : collide_fn<true, false, false>();
-  }
-  if (th) return ex ? collide_fn<false, true, true>() : collide_fn<false, true, false>();
-  return ex ? collide_fn<false, false, true>() : collide_fn<false, false, false>();
-}
-
-size_t collide_smem_bytes(bool mixed, int cap, int bcap) {
-  size_t off[8];
-  return mixed ? collide_smem_layout<true>(cap, bcap, off) : collide_smem_layout<false>(cap, bcap, off);
-}
-
-cudaError_t prepare_collide(bool mixed, size_t smem) {
-  for (int v = 0; v < 4; ++v) {
-    cudaError_t e = cudaFuncSetAttribute(collide_variant(mixed, v),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-int collide_blocks_per_sm(bool mixed, int variant, size_t smem) {
-  int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, collide_variant(mixed, variant), BLOCK, smem);
-  return nb;
-}
-
-void launch_collide(bool mixed, int variant, const BoxDev* boxes, const int2* tiles, int ntiles,
-                    int grid, int cap, int bcap, size_t smem, int2* ovf, int* novf, int* err,
-                    cudaStream_t s) {
-  if (ntiles <= 0) return;
-  void* args[] = {(void*)&boxes, (void*)&tiles, (void*)&ntiles, (void*)&cap, (void*)&bcap,
-                  (void*)&ovf, (void*)&novf, (void*)&err};
-  cudaLaunchKernel(collide_variant(mixed, variant), dim3(grid), dim3(BLOCK), args, smem, s);
-}
-
-void launch_collide_overflow(bool mixed, const BoxDev* boxes, const int2* ovf, const int* novf,
-                             int grid, int* err, cudaStream_t s) {
-  if (mixed) k_collide_overflow<true><<<grid, BLOCK, 0, s>>>(boxes, ovf, novf, err);
-  else k_collide_overflow<false><<<grid, BLOCK, 0, s>>>(boxes, ovf, novf, err);
-}
 
 }  // namespace mpcd

@@ -1,0 +1,426 @@
+// k_cells.cu -- the fused SRD step on cell rows (arXiv:1801.10187: Sec. 2
+// Eqs. stream, srd and thermo; Sec. 3.4 cell list; Sec. 3.5 cell properties;
+// Sec. 3.6 rotation and thermostat, algorithm "SRD collision rule").
+//
+// One thread owns one cell.  Its members are the records of its row (plus,
+// rarely, overflow records).  Mode F is one whole step boundary in one pass:
+//   collide step t      pass 1 forms the exact cell sums (and, with the
+//                       thermostat, a second pass the energy about u); the
+//                       thread draws the axis and xi; pass 2 rotates each member
+//   stream step t + 1   the rotated velocity streams the position
+//   bin step t + 1      with the next grid shift; the record is appended to the
+//                       row of its new cell in the other buffer (atomic slot)
+// Mode P only streams and bins (the first step after the state was read or
+// set), mode C only collides, in place (to complete a step before the state is
+// read).  Nothing else touches the particles: no separate sort, scan or
+// reorder pass exists, and every record moves as one 32-byte sector.
+#include "dev_collide.cuh"
+#include "dev_stream.cuh"
+#include "kernels.h"
+#include "mpcd_internal.cuh"
+
+namespace mpcd {
+
+template <bool MIXED>
+using rec_t = typename std::conditional<MIXED, RecF, RecD>::type;
+
+__device__ __forceinline__ void load_rec(const RecF* p, float r[3], float v[3], uint32_t& tag) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0];
+  const float4 b = reinterpret_cast<const float4*>(p)[1];
+  r[0] = a.x; r[1] = a.y; r[2] = a.z;
+  v[0] = a.w; v[1] = b.x; v[2] = b.y;
+  tag = __float_as_uint(b.z);
+}
+__device__ __forceinline__ void store_rec(RecF* p, const float r[3], const float v[3], uint32_t tag) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(r[0], r[1], r[2], v[0]);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[1], v[2], __uint_as_float(tag), 0.0f);
+}
+__device__ __forceinline__ void load_rec(const RecD* p, double r[3], double v[3], uint32_t& tag) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  const double2 c = reinterpret_cast<const double2*>(p)[2];
+  const uint4 d = reinterpret_cast<const uint4*>(p)[3];
+  r[0] = a.x; r[1] = a.y; r[2] = b.x;
+  v[0] = b.y; v[1] = c.x; v[2] = c.y;
+  tag = d.x;
+}
+__device__ __forceinline__ void store_rec(RecD* p, const double r[3], const double v[3], uint32_t tag) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(r[0], r[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(r[2], v[0]);
+  reinterpret_cast<double2*>(p)[2] = make_double2(v[1], v[2]);
+  reinterpret_cast<uint4*>(p)[3] = make_uint4(tag, 0u, 0u, 0u);
+}
+__device__ __forceinline__ void load_v(const RecF* p, float v[3]) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0];
+  const float2 b = reinterpret_cast<const float2*>(p)[2];
+  v[0] = a.w; v[1] = b.x; v[2] = b.y;
+}
+__device__ __forceinline__ void load_v(const RecD* p, double v[3]) {
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  const double2 c = reinterpret_cast<const double2*>(p)[2];
+  v[0] = b.y; v[1] = c.x; v[2] = c.y;
+}
+
+// Append a record to the row of cell c in the output set (or to the output
+// overflow list when the row is full).
+template <bool MIXED>
+__device__ __forceinline__ void insert(const BoxDev& B, int out, uint32_t c,
+                                       const real_t<MIXED> r[3], const real_t<MIXED> v[3],
+                                       uint32_t tag, int* err) {
+  using R = rec_t<MIXED>;
+  const uint32_t slot = atomicAdd(&B.cnt[out][c], 1u);
+  if (slot < (uint32_t)B.K) {
+    store_rec(((R*)B.rows[out]) + (size_t)c * B.K + slot, r, v, tag);
+  } else {
+    const uint32_t j = atomicAdd(&B.ovf_n[out], 1u);
+    if (j < (uint32_t)B.ovf_cap) {
+      store_rec(((R*)B.ovf_rec[out]) + j, r, v, tag);
+      B.ovf_cell[out][j] = c;
+    } else {
+      atomicOr(err, ERR_OVERFLOW_CAP);
+    }
+  }
+}
+
+template <bool MIXED, bool THERMO, bool EXTRA, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxes,
+                                                 const int2* __restrict__ spans, int nspans,
+                                                 int* err) {
+  using T = real_t<MIXED>;
+  using R = rec_t<MIXED>;
+  __shared__ long long sSn[3];  // shift of the step the records are binned for
+  __shared__ long long sSz;     // z shift of the collision step (wall-cut cells)
+  for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
+    const int2 tt = spans[sp];
+    const BoxDev& B = boxes[tt.x];
+    const unsigned long long t = B.step;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (MODE != MODE_C) shift_units(B, MODE == MODE_P ? t : t + 1ull, sSn);
+      if (EXTRA && MODE != MODE_P) {
+        long long S[3];
+        shift_units(B, t, S);
+        sSz = S[2];
+      }
+    }
+    __syncthreads();
+    const int cell = tt.y + (int)threadIdx.x;
+    if (cell >= B.ncells) continue;
+    const int cur = B.cur, out = cur ^ 1;
+    const int K = B.K;
+    const uint32_t n = B.cnt[cur][cell];
+    if (MODE != MODE_C && n) B.cnt[cur][cell] = 0u;  // this set is written two steps on
+    const int nrow = (int)n < K ? (int)n : K;
+    const bool has_ovf = (int)n > K;
+    R* row = ((R*)B.rows[cur]) + (size_t)cell * K;
+    R* ovf = (R*)B.ovf_rec[cur];
+    const uint32_t* ovf_cell = B.ovf_cell[cur];
+    const uint32_t novf = has_ovf ? B.ovf_n[cur] : 0u;
+    int b0 = 0, nbt = 0;
+    if (EXTRA && MODE != MODE_P && B.nbead > 0) {
+      const int g = cell / B.tc;
+      b0 = (int)B.bstart[g];
+      nbt = (int)B.bstart[g + 1] - b0;
+    }
+    auto bead_in = [&](int j, int& b) {
+      b = (int)B.border[b0 + j];
+      return B.bcell[b] == cell;
+    };
+    bool any = n > 0;
+    if (EXTRA)
+      for (int j = 0; j < nbt && !any; ++j) {
+        int b;
+        any = bead_in(j, b);
+      }
+    if (!any) continue;
+
+    CellParams<T> prm;
+    if (MODE != MODE_P) {
+      // ---- cell properties (Sec. 3.5) ----
+      CellAcc<MIXED> a;
+#pragma unroll 4
+      for (int k = 0; k < nrow; ++k) {
+        T w[3];
+        load_v(row + k, w);
+        a.add_solvent(B, w);
+      }
+      if (has_ovf)
+        for (uint32_t j = 0; j < novf; ++j)
+          if (ovf_cell[j] == (uint32_t)cell) {
+            T w[3];
+            load_v(ovf + j, w);
+            a.add_solvent(B, w);
+          }
+      auto solvent_energy = [&](const T u[3], CellAcc<MIXED>& acc) {
+#pragma unroll 4
+        for (int k = 0; k < nrow; ++k) {
+          T w[3];
+          load_v(row + k, w);
+          acc.add_solvent_energy(B, w, u);
+        }
+        if (has_ovf)
+          for (uint32_t j = 0; j < novf; ++j)
+            if (ovf_cell[j] == (uint32_t)cell) {
+              T w[3];
+              load_v(ovf + j, w);
+              acc.add_solvent_energy(B, w, u);
+            }
+      };
+      const double sz = EXTRA ? (double)sSz * 0x1p-32 : 0.0;
+      T u[3];
+      cell_mean<MIXED>(B, t, (uint32_t)cell, sz, a, EXTRA ? nbt : 0, bead_in, EXTRA, u);
+      if (THERMO) solvent_energy(u, a);
+      cell_finish<MIXED>(B, t, (uint32_t)cell, a, u, EXTRA ? nbt : 0, bead_in, THERMO, EXTRA, prm,
+                         err);
+    }
+
+    // ---- members: collide, then stream and bin for the next step ----
+    auto process = [&](R* p) {
+      T r[3], w[3];
+      uint32_t tag;
+      load_rec(p, r, w, tag);
+      if (MODE != MODE_P) collide_one<MIXED>(B, prm, w, THERMO);
+      if (MODE == MODE_C) {
+        store_rec(p, r, w, tag);
+        return;
+      }
+      stream_one(B, r, w);
+      const uint32_t c2 = cell_of(B, sSn, r, err);
+      insert<MIXED>(B, out, c2, r, w, tag, err);
+    };
+#pragma unroll 2
+    for (int k = 0; k < nrow; ++k) process(row + k);
+    if (has_ovf)
+      for (uint32_t j = 0; j < novf; ++j)
+        if (ovf_cell[j] == (uint32_t)cell) process(ovf + j);
+    if (EXTRA && MODE != MODE_P) {
+      for (int j = 0; j < nbt; ++j) {
+        int b;
+        if (!bead_in(j, b)) continue;
+        double w[3] = {B.svel[3 * b], B.svel[3 * b + 1], B.svel[3 * b + 2]};
+        collide_bead<MIXED>(B, prm, w, THERMO);
+        B.svel[3 * b] = w[0];
+        B.svel[3 * b + 1] = w[1];
+        B.svel[3 * b + 2] = w[2];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// State in and out.  The input is placed in the rows of the unshifted grid
+// (any placement works: the next step re-bins after streaming).  Positions
+// are stored as given; only the placement uses a wrapped copy.
+// ---------------------------------------------------------------------------
+template <bool MIXED>
+__global__ void k_load(const BoxDev* __restrict__ box, const real_t<MIXED>* __restrict__ pos,
+                       const real_t<MIXED>* __restrict__ vel, int* err) {
+  using T = real_t<MIXED>;
+  const BoxDev& B = *box;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.nsol; i += gridDim.x * blockDim.x) {
+    const T r[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    const T v[3] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2]};
+    int c[3];
+    for (int k = 0; k < 3; ++k) {
+      const double L = B.L[k];
+      double x = (double)r[k];
+      x = x - L * floor(x / L);
+      int q = (x >= 0.0 && x < L) ? (int)x : 0;
+      if (q >= B.n[k]) q = B.n[k] - 1;
+      c[k] = q;
+    }
+    if (B.walls) c[2] += 1;  // channel layers are 1 .. n_z of the n_z + 2 layers
+    const uint32_t cell = (uint32_t)(c[0] + B.n[0] * (c[1] + B.n[1] * c[2]));
+    insert<MIXED>(B, B.cur, cell, r, v, (uint32_t)i, err);
+  }
+}
+
+// Records of the current set, written in input order; cell_out (optional)
+// receives each particle's cell.
+template <bool MIXED>
+__global__ void k_extract(const BoxDev* __restrict__ box, real_t<MIXED>* __restrict__ pos,
+                          real_t<MIXED>* __restrict__ vel, int32_t* __restrict__ cell_out) {
+  using T = real_t<MIXED>;
+  using R = rec_t<MIXED>;
+  const BoxDev& B = *box;
+  const int cur = B.cur;
+  const int stride = gridDim.x * blockDim.x;
+  const int K = B.K;
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < B.ncells; cell += stride) {
+    const uint32_t n = B.cnt[cur][cell];
+    const int nrow = (int)n < K ? (int)n : K;
+    const R* row = ((const R*)B.rows[cur]) + (size_t)cell * K;
+    for (int k = 0; k < nrow; ++k) {
+      T r[3], v[3];
+      uint32_t tag;
+      load_rec(row + k, r, v, tag);
+      for (int q = 0; q < 3; ++q) {
+        pos[3 * tag + q] = r[q];
+        vel[3 * tag + q] = v[q];
+      }
+      if (cell_out) cell_out[tag] = cell;
+    }
+  }
+  const uint32_t novf = B.ovf_n[cur];
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < novf; j += stride) {
+    T r[3], v[3];
+    uint32_t tag;
+    load_rec(((const R*)B.ovf_rec[cur]) + j, r, v, tag);
+    for (int q = 0; q < 3; ++q) {
+      pos[3 * tag + q] = r[q];
+      vel[3 * tag + q] = v[q];
+    }
+    if (cell_out) cell_out[tag] = (int32_t)B.ovf_cell[cur][j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+template <bool M, bool TH, bool EX, int MODE>
+static void* cells_fn() {
+  return (void*)k_cells<M, TH, EX, MODE>;
+}
+
+template <int MODE>
+static void* cells_variant_mode(bool mixed, int variant) {
+  const bool th = (variant & 1) != 0, ex = (variant & 2) != 0;
+  if (mixed) {
+    if (th) return ex ? cells_fn<true, true, true, MODE>() : cells_fn<true, true, false, MODE>();
+    return ex ? cells_fn<true, false, true, MODE>() : cells_fn<true, false, false, MODE>();
+  }
+  if (th) return ex ? cells_fn<false, true, true, MODE>() : cells_fn<false, true, false, MODE>();
+  return ex ? cells_fn<false, false, true, MODE>() : cells_fn<false, false, false, MODE>();
+}
+
+static void* cells_variant(bool mixed, int variant, int mode) {
+  if (mode == MODE_P) return cells_variant_mode<MODE_P>(mixed, variant);
+  if (mode == MODE_F) return cells_variant_mode<MODE_F>(mixed, variant);
+  return cells_variant_mode<MODE_C>(mixed, variant);
+}
+
+int cells_blocks_per_sm(bool mixed, int variant, int mode) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cells_variant(mixed, variant, mode), BLOCK, 0);
+  return nb;
+}
+
+void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const int2* spans,
+                  int nspans, int grid, int* err, cudaStream_t s) {
+  if (nspans <= 0) return;
+  void* args[] = {(void*)&boxes, (void*)&spans, (void*)&nspans, (void*)&err};
+  cudaLaunchKernel(cells_variant(mixed, variant, mode), dim3(grid), dim3(BLOCK), args, 0, s);
+}
+
+static int grid_for_n(int n) {
+  int g = (n + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 8192) g = 8192;
+  return g;
+}
+
+void launch_load(bool mixed, const BoxDev* box, const void* pos, const void* vel, int n, int* err,
+                 cudaStream_t s) {
+  if (n <= 0) return;
+  if (mixed)
+    k_load<true><<<grid_for_n(n), 256, 0, s>>>(box, (const float*)pos, (const float*)vel, err);
+  else
+    k_load<false><<<grid_for_n(n), 256, 0, s>>>(box, (const double*)pos, (const double*)vel, err);
+}
+
+void launch_extract(bool mixed, const BoxDev* box, void* pos, void* vel, int32_t* cell_out,
+                    int ncells, cudaStream_t s) {
+  if (mixed)
+    k_extract<true><<<grid_for_n(ncells), 256, 0, s>>>(box, (float*)pos, (float*)vel, cell_out);
+  else
+    k_extract<false><<<grid_for_n(ncells), 256, 0, s>>>(box, (double*)pos, (double*)vel, cell_out);
+}
+
+}  // namespace mpcd
+
+namespace mpcd {
+
+// ---------------------------------------------------------------------------
+// Thermal initial state drawn on the device (input generation for batched and
+// served jobs, not part of a step): positions uniform in the box, velocity
+// components Gaussian with variance kT/m (Box-Muller), then the mean velocity
+// removed, as the benchmark set-up of Sec. 4 / 4.1 does.  Particle i uses
+// counters (i, 0..2) under its own purpose; the mean comes from exact int64
+// fixed-point sums, so the state is reproducible.
+// ---------------------------------------------------------------------------
+constexpr uint32_t PURPOSE_INIT = 0x494E4954u;
+
+struct InitParams {
+  uint32_t seed_lo, seed_hi;
+  double L[3];
+  double sigma;
+  int n;
+};
+
+__device__ __forceinline__ void init_draw(const InitParams& P, int i, double r[3], double v[3]) {
+  const uint2 key = make_uint2(P.seed_lo, P.seed_hi ^ PURPOSE_INIT);
+  const uint4 a = philox(make_uint4((uint32_t)i, 0u, 0u, 0u), key);
+  const uint4 b = philox(make_uint4((uint32_t)i, 1u, 0u, 0u), key);
+  const uint4 c = philox(make_uint4((uint32_t)i, 2u, 0u, 0u), key);
+  r[0] = P.L[0] * ((double)a.x * 0x1p-32);
+  r[1] = P.L[1] * ((double)a.y * 0x1p-32);
+  r[2] = P.L[2] * ((double)a.z * 0x1p-32);
+  const double u1 = unit53(b.x, b.y), u2 = unit53(b.z, b.w);
+  const double u3 = unit53(c.x, c.y), u4 = unit53(c.z, c.w);
+  const double rho1 = sqrt(-2.0 * log(1.0 - u1)), rho2 = sqrt(-2.0 * log(1.0 - u3));
+  v[0] = P.sigma * (rho1 * cos(kTwoPi * u2));
+  v[1] = P.sigma * (rho1 * sin(kTwoPi * u2));
+  v[2] = P.sigma * (rho2 * cos(kTwoPi * u4));
+}
+
+__global__ void k_init_sum(InitParams P, unsigned long long* sums) {
+  long long s[3] = {0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    double r[3], v[3];
+    init_draw(P, i, r, v);
+    for (int k = 0; k < 3; ++k) s[k] += __double2ll_rn(v[k] * 4294967296.0);
+  }
+  for (int k = 0; k < 3; ++k) {
+    long long x = s[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&sums[k], (unsigned long long)x);
+  }
+}
+
+template <bool MIXED>
+__global__ void k_init_write(InitParams P, const unsigned long long* sums, real_t<MIXED>* pos,
+                             real_t<MIXED>* vel) {
+  using T = real_t<MIXED>;
+  double mean[3];
+  for (int k = 0; k < 3; ++k)
+    mean[k] = P.n > 0 ? ((double)(long long)sums[k] * 0x1p-32) / (double)P.n : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    double r[3], v[3];
+    init_draw(P, i, r, v);
+    for (int k = 0; k < 3; ++k) {
+      T x = (T)r[k];
+      if (!((double)x < P.L[k])) x = (T)0;  // rounding up to L wraps to 0
+      pos[3 * i + k] = x;
+      vel[3 * i + k] = (T)(v[k] - mean[k]);
+    }
+  }
+}
+
+void launch_init_thermal(bool mixed, int n, uint64_t seed, const double L[3], double sigma,
+                         void* pos, void* vel, unsigned long long* sums, cudaStream_t s) {
+  if (n <= 0) return;
+  InitParams P;
+  P.seed_lo = (uint32_t)seed;
+  P.seed_hi = (uint32_t)(seed >> 32);
+  for (int k = 0; k < 3; ++k) P.L[k] = L[k];
+  P.sigma = sigma;
+  P.n = n;
+  int g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  cudaMemsetAsync(sums, 0, 3 * sizeof(unsigned long long), s);
+  k_init_sum<<<g, 256, 0, s>>>(P, sums);
+  if (mixed) k_init_write<true><<<g, 256, 0, s>>>(P, sums, (float*)pos, (float*)vel);
+  else k_init_write<false><<<g, 256, 0, s>>>(P, sums, (double*)pos, (double*)vel);
+}
+
+}  // namespace mpcd

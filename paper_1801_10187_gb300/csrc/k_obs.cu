@@ -1,6 +1,7 @@
 // k_obs.cu -- observables (arXiv:1801.10187, Sec. 3.5 last paragraph: net
 // momentum, energy and temperature), the z profile of v_x used for the
-// Poiseuille check, and state movement (tag order out, last-step cell ids).
+// Poiseuille check, and the member counts of the last step.  They read the
+// state in input order, as k_extract writes it.
 #include <type_traits>
 
 #include "kernels.h"
@@ -11,29 +12,23 @@ namespace mpcd {
 template <bool MIXED>
 using real_t = typename std::conditional<MIXED, float, double>::type;
 
-__global__ void k_iota(uint32_t* a, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    a[i] = (uint32_t)i;
-}
-
 // Per-particle pass: block partial sums of P and KE (double, fixed block
 // decomposition) and fixed-point sums per cell of the unshifted grid.
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_obs_particles(const BoxDev* __restrict__ box, ObsCells oc,
-                                                       double* __restrict__ partials) {
-  using T = real_t<MIXED>;
+__global__ void __launch_bounds__(256) k_obs_particles(const BoxDev* __restrict__ box,
+                                                       const real_t<MIXED>* __restrict__ pos,
+                                                       const real_t<MIXED>* __restrict__ vel,
+                                                       ObsCells oc, double* __restrict__ partials) {
   const BoxDev& B = *box;
   __shared__ double red[4][256];
   double acc[4] = {0, 0, 0, 0};
   const int ntot = B.nsol + B.nbead;
-  const T* r = (const T*)B.r;
-  const T* v = (const T*)B.v;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += gridDim.x * blockDim.x) {
     double x[3], w[3], m;
     if (i < B.nsol) {
       for (int k = 0; k < 3; ++k) {
-        x[k] = (double)r[3 * i + k];
-        w[k] = (double)v[3 * i + k];
+        x[k] = (double)pos[3 * i + k];
+        w[k] = (double)vel[3 * i + k];
       }
       m = B.m;
     } else {
@@ -104,53 +99,25 @@ __global__ void __launch_bounds__(256) k_obs_cells(ObsCells oc, double* __restri
 }
 
 template <bool MIXED>
-__global__ void k_profile(const BoxDev* __restrict__ box, int nbins, double* sum,
-                          unsigned long long* cnt, double H) {
-  using T = real_t<MIXED>;
-  const BoxDev& B = *box;
-  const T* r = (const T*)B.r;
-  const T* v = (const T*)B.v;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.nsol; i += gridDim.x * blockDim.x) {
-    long long b = (long long)floor((double)r[3 * i + 2] / H * (double)nbins);
+__global__ void k_profile(const real_t<MIXED>* __restrict__ pos, const real_t<MIXED>* __restrict__ vel,
+                          int n, int nbins, double* sum, unsigned long long* cnt, double H) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    long long b = (long long)floor((double)pos[3 * i + 2] / H * (double)nbins);
     if (b < 0) b = 0;
     if (b >= nbins) b = nbins - 1;
-    atomicAdd(&sum[b], (double)v[3 * i]);
+    atomicAdd(&sum[b], (double)vel[3 * i]);
     atomicAdd(&cnt[b], 1ull);
   }
 }
 
-// Write the state in tag (input) order into r2 / v2.
-template <bool MIXED>
-__global__ void k_unpermute(const BoxDev* __restrict__ box) {
-  using T = real_t<MIXED>;
+// Member counts of the current cells: solvent from the row counts, then the
+// beads of the step.
+__global__ void k_cell_counts(const BoxDev* __restrict__ box, int32_t* count_out) {
   const BoxDev& B = *box;
-  const T* r = (const T*)B.r;
-  const T* v = (const T*)B.v;
-  T* r2 = (T*)B.r2;
-  T* v2 = (T*)B.v2;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < B.nsol; k += gridDim.x * blockDim.x) {
-    const uint32_t g = B.tag[k];
-    for (int q = 0; q < 3; ++q) {
-      r2[3 * g + q] = r[3 * k + q];
-      v2[3 * g + q] = v[3 * k + q];
-    }
-  }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < B.ncells; c += gridDim.x * blockDim.x)
+    count_out[c] = (int32_t)B.cnt[B.cur][c];
 }
-
-// Cell of every particle at the last completed step, in tag order, and the
-// member count of every cell.  key[] is indexed by the storage slot the
-// particle had when it was binned, whose tag is in tag2 after a reorder.
-__global__ void k_last_cells(const BoxDev* __restrict__ box, int32_t* cell_out, int32_t* count_out) {
-  const BoxDev& B = *box;
-  const uint32_t* tg = B.permuted ? B.tag2 : B.tag;
-  const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.nsol; i += stride)
-    if (cell_out) cell_out[tg[i]] = (int32_t)(B.key[i] >> 32);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < B.ncells; c += stride)
-    if (count_out) count_out[c] = (int32_t)(B.start[c + 1] - B.start[c]);
-}
-__global__ void k_last_cells_beads(const BoxDev* __restrict__ box, int32_t* cell_out,
-                                   int32_t* count_out) {
+__global__ void k_bead_cells(const BoxDev* __restrict__ box, int32_t* cell_out, int32_t* count_out) {
   const BoxDev& B = *box;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B.nbead; b += gridDim.x * blockDim.x) {
     const int32_t c = B.bcell[b];
@@ -166,39 +133,30 @@ static int grid_for(int n, int per_block) {
   return g;
 }
 
-void launch_iota(uint32_t* a, int n, cudaStream_t s) {
-  if (n <= 0) return;
-  k_iota<<<grid_for(n, 256), 256, 0, s>>>(a, n);
-}
-
-void launch_obs_particles(bool mixed, const BoxDev* box, ObsCells oc, double* partials, int nblocks,
-                          cudaStream_t s) {
-  if (mixed) k_obs_particles<true><<<nblocks, 256, 0, s>>>(box, oc, partials);
-  else k_obs_particles<false><<<nblocks, 256, 0, s>>>(box, oc, partials);
+void launch_obs_particles(bool mixed, const BoxDev* box, const void* pos, const void* vel,
+                          ObsCells oc, double* partials, int nblocks, cudaStream_t s) {
+  if (mixed)
+    k_obs_particles<true><<<nblocks, 256, 0, s>>>(box, (const float*)pos, (const float*)vel, oc, partials);
+  else
+    k_obs_particles<false><<<nblocks, 256, 0, s>>>(box, (const double*)pos, (const double*)vel, oc,
+                                                   partials);
 }
 
 void launch_obs_cells(ObsCells oc, double* partials, int nblocks, cudaStream_t s) {
   k_obs_cells<<<nblocks, 256, 0, s>>>(oc, partials);
 }
 
-void launch_profile(bool mixed, const BoxDev* box, int nbins, double* sum, unsigned long long* cnt,
-                    int n, double H, cudaStream_t s) {
+void launch_profile(bool mixed, const void* pos, const void* vel, int n, int nbins, double* sum,
+                    unsigned long long* cnt, double H, cudaStream_t s) {
   const int g = grid_for(n, 256);
-  if (mixed) k_profile<true><<<g, 256, 0, s>>>(box, nbins, sum, cnt, H);
-  else k_profile<false><<<g, 256, 0, s>>>(box, nbins, sum, cnt, H);
+  if (mixed) k_profile<true><<<g, 256, 0, s>>>((const float*)pos, (const float*)vel, n, nbins, sum, cnt, H);
+  else k_profile<false><<<g, 256, 0, s>>>((const double*)pos, (const double*)vel, n, nbins, sum, cnt, H);
 }
 
-void launch_unpermute(bool mixed, const BoxDev* box, int n, cudaStream_t s) {
-  if (n <= 0) return;
-  if (mixed) k_unpermute<true><<<grid_for(n, 256), 256, 0, s>>>(box);
-  else k_unpermute<false><<<grid_for(n, 256), 256, 0, s>>>(box);
-}
-
-void launch_last_cells(const BoxDev* box, int nsol, int nbead, int ncells, int32_t* cell_out,
-                       int32_t* count_out, cudaStream_t s) {
-  const int n = nsol > ncells ? nsol : ncells;
-  k_last_cells<<<grid_for(n, 256), 256, 0, s>>>(box, cell_out, count_out);
-  if (nbead > 0) k_last_cells_beads<<<grid_for(nbead, 256), 256, 0, s>>>(box, cell_out, count_out);
+void launch_cell_counts(const BoxDev* box, int ncells, int nbead, int32_t* cell_out,
+                        int32_t* count_out, cudaStream_t s) {
+  if (count_out) k_cell_counts<<<grid_for(ncells, 256), 256, 0, s>>>(box, count_out);
+  if (nbead > 0) k_bead_cells<<<grid_for(nbead, 256), 256, 0, s>>>(box, cell_out, count_out);
 }
 
 }  // namespace mpcd

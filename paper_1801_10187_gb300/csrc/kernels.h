@@ -7,32 +7,36 @@
 
 namespace mpcd {
 
-void launch_stream_bin(bool mixed, const BoxDev* boxes, const int2* tiles, int ntiles, int grid,
-                       int* err, cudaStream_t s);
+// ---- fused step on cell rows (k_cells.cu) ----
+// mode: MODE_P stream + bin, MODE_F collide + stream + bin, MODE_C collide in place.
+// variant = (thermostat ? 1 : 0) | (solute beads or walls ? 2 : 0).
+int cells_blocks_per_sm(bool mixed, int variant, int mode);
+void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const int2* spans,
+                  int nspans, int grid, int* err, cudaStream_t s);
+// Place n particles (device arrays of float (mixed) or double, n x 3) in the
+// current rows of a box whose counts are zero.
+void launch_load(bool mixed, const BoxDev* box, const void* pos, const void* vel, int n, int* err,
+                 cudaStream_t s);
+// Current state into device arrays in input order (cell_out optional).
+void launch_extract(bool mixed, const BoxDev* box, void* pos, void* vel, int32_t* cell_out,
+                    int ncells, cudaStream_t s);
+
+// Thermal initial state drawn on the device into pos/vel (n x 3 of the storage
+// type); sums: 3 device words of scratch.
+void launch_init_thermal(bool mixed, int n, uint64_t seed, const double L[3], double sigma,
+                         void* pos, void* vel, unsigned long long* sums, cudaStream_t s);
+
+// ---- solute and pass bookkeeping (k_step.cu) ----
 void launch_md_bin(const BoxDev* boxes, const int2* tiles, int ntiles, int chains_per_block,
                    int threads, int* err, cudaStream_t s);
 void launch_scan(const ScanSeg* segs, const int2* tiles, int ntiles, uint32_t* tsum,
                  unsigned long long* gscan, uint32_t* toff, int grid, cudaStream_t s);
-void launch_scatter(const BoxDev* boxes, const int2* tiles, int ntiles, int grid, cudaStream_t s);
 void launch_bead_scatter(const BoxDev* boxes, const int2* tiles, int ntiles, cudaStream_t s);
-// reorder every sort_period steps, then swap the buffers in (two launches)
-void launch_permute(bool mixed, BoxDev* boxes, int nboxes, const int2* tiles, int ntiles,
-                    int grid, cudaStream_t s);
-// advance the step counters and clear the overflow queue
-void launch_end_step(BoxDev* boxes, int nboxes, int* novf, cudaStream_t s);
+// flip: the output set becomes current (after modes P and F); advance: step += 1
+// (after modes F and C).
+void launch_after_pass(BoxDev* boxes, int nboxes, bool flip, bool advance, cudaStream_t s);
 
-size_t collide_smem_bytes(bool mixed, int cap, int bcap);
-cudaError_t prepare_collide(bool mixed, size_t smem);
-// variant = (thermostat ? 1 : 0) | (solute beads or walls ? 2 : 0)
-int collide_blocks_per_sm(bool mixed, int variant, size_t smem);
-void launch_collide(bool mixed, int variant, const BoxDev* boxes, const int2* tiles, int ntiles,
-                    int grid, int cap, int bcap, size_t smem, int2* ovf, int* novf, int* err,
-                    cudaStream_t s);
-// tiles the fast path queued in ovf[0 .. *novf)
-void launch_collide_overflow(bool mixed, const BoxDev* boxes, const int2* ovf, const int* novf,
-                             int grid, int* err, cudaStream_t s);
-
-// observables / diagnostics / state movement (k_obs.cu)
+// ---- observables (k_obs.cu) ----
 struct ObsCells {
   uint32_t* cnt;
   long long* mass;
@@ -40,14 +44,12 @@ struct ObsCells {
   long long* k;
   int ncells;
 };
-void launch_iota(uint32_t* a, int n, cudaStream_t s);
-void launch_obs_particles(bool mixed, const BoxDev* box, ObsCells oc, double* partials,
-                          int nblocks, cudaStream_t s);
+void launch_obs_particles(bool mixed, const BoxDev* box, const void* pos, const void* vel,
+                          ObsCells oc, double* partials, int nblocks, cudaStream_t s);
 void launch_obs_cells(ObsCells oc, double* partials, int nblocks, cudaStream_t s);
-void launch_profile(bool mixed, const BoxDev* box, int nbins, double* sum, unsigned long long* cnt,
-                    int n, double H, cudaStream_t s);
-void launch_unpermute(bool mixed, const BoxDev* box, int n, cudaStream_t s);
-void launch_last_cells(const BoxDev* box, int nsol, int nbead, int ncells, int32_t* cell_out,
-                       int32_t* count_out, cudaStream_t s);
+void launch_profile(bool mixed, const void* pos, const void* vel, int n, int nbins, double* sum,
+                    unsigned long long* cnt, double H, cudaStream_t s);
+void launch_cell_counts(const BoxDev* box, int ncells, int nbead, int32_t* cell_out,
+                        int32_t* count_out, cudaStream_t s);
 
 }  // namespace mpcd

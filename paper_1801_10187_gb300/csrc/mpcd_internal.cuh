@@ -1,18 +1,15 @@
 // mpcd_internal.cuh -- device-side data layout and small device helpers of
 // libmpcd (SRD step of arXiv:1801.10187 on one GB300, sm_103a).
 //
-// Layout in HBM, per box (Sec. 3.2 particle data, re-laid for GB300):
-//   r, v      : packed xyz (3 x float in the mixed model, 3 x double in FP64),
-//               12 / 24 bytes per particle, no padding lane
-//   r2, v2    : second copies used by the periodic reorder (Sec. 3.8) and as
-//               scratch for tag-order output
-//   tag, tag2 : uint32 input index of the particle at each storage slot
-//   key       : uint64 (cell << 32 | slot-in-cell) written by binning
-//   order     : uint32 storage index of every sorted position (cell order)
-//   count     : uint32 per-cell histogram of the step (zeroed by the scan)
-//   start     : uint32 per-cell exclusive prefix sum, ncells + 1 entries
-// Solute beads (double) have their own short arrays; they are ordered per
-// collision tile rather than per cell.
+// Layout in HBM, per box (Sec. 3.2 particle data and Sec. 3.4 cell list,
+// re-laid for GB300): the particles live in their cells.  Cell c owns a row of
+// K records; a record is one particle (position, velocity, input index) and
+// is 32 bytes in the mixed model -- exactly one DRAM sector -- or 64 bytes in
+// FP64.  cnt[c] counts the cell's members; members beyond K sit in an
+// overflow list with their cell id.  Rows, counts and overflow lists are
+// double buffered: the fused step reads one set (cells of step t) and
+// writes the other (cells of step t + 1).  Solute beads (double) have their
+// own arrays, grouped per tile of 32 cells.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -29,9 +26,25 @@ constexpr uint32_t PURPOSE_VIRT = 0x56495254u;
 constexpr int ERR_GAMMA_CAP = 1;   // thermostat sampler rejected 64 times
 constexpr int ERR_CELL_RANGE = 2;  // a cell id left the grid (non-finite position)
 
-constexpr int PTILE = 1024;    // particles per streaming / scatter tile
+constexpr int PTILE = 1024;    // particles per tile of the particle-parallel kernels
 constexpr int STILE = 2048;    // entries per scan tile
-constexpr int BLOCK = 256;     // threads per block of the tile kernels
+constexpr int BLOCK = 256;     // threads per block; the fused step has one thread per cell
+constexpr int BEAD_TILE = 32;  // cells per bead group
+constexpr int ERR_OVERFLOW_CAP = 4;  // overflow list full (cannot happen: it holds N records)
+
+// Passes of the fused step kernel.
+enum { MODE_P = 0, MODE_F = 1, MODE_C = 2 };
+
+// One particle (mixed model: 32 bytes, FP64: 64 bytes).
+struct __align__(16) RecF {
+  float x, y, z, vx, vy, vz;
+  uint32_t tag, pad;
+};
+struct __align__(16) RecD {
+  double x, y, z, vx, vy, vz;
+  uint32_t tag, pad;
+  uint64_t pad2;
+};
 
 struct BoxDev {
   // geometry and sizes
@@ -44,9 +57,10 @@ struct BoxDev {
   int32_t md_substeps;
   int32_t thermostat;
   int32_t walls;
-  int32_t sort_period;  // > 0: reorder when step % sort_period == 0
-  int32_t tc;           // cells per collision tile
-  int32_t nctiles;      // collision tiles of this box
+  int32_t K;            // records per cell row
+  int32_t ovf_cap;      // capacity of each overflow list
+  int32_t tc;           // cells per bead group (BEAD_TILE)
+  int32_t nctiles;      // bead groups of this box
   uint32_t seed_lo, seed_hi;
   // parameters, double
   double dt, kT, m, Mb, bond_k, bond_r0, virt_density, sigma_virt;
@@ -56,26 +70,23 @@ struct BoxDev {
   // parameters, float (mixed model)
   float dt_f, kT_f, m_f, Mb_f, ca_f, sa_f, omc_f, pad_f;
   float g_f[3], hg_f[3], gdt_f[3], L_f[3];
-  // state; the pointers and counters below are updated on the device
-  void* r;
-  void* v;
-  void* r2;
-  void* v2;
-  uint32_t* tag;
-  uint32_t* tag2;
-  uint64_t* key;
-  uint32_t* order;
-  uint32_t* count;
-  uint32_t* start;
+  // particle storage (double buffered; cur selects the current set)
+  void* rows[2];        // ncells * K records
+  uint32_t* cnt[2];     // members per cell
+  void* ovf_rec[2];     // overflow records
+  uint32_t* ovf_cell[2];
+  uint32_t* ovf_n;      // two counters
+  // solute
   double* spos;
   double* svel;
   int32_t* bcell;   // bead cell id of the current step
-  uint64_t* bkey;   // bead (tile << 32 | slot)
-  uint32_t* border; // bead indices grouped by collision tile
-  uint32_t* bcount; // per collision tile bead histogram
+  uint64_t* bkey;   // bead (group << 32 | slot)
+  uint32_t* border; // bead indices grouped by bead group
+  uint32_t* bcount; // per bead group histogram
   uint32_t* bstart; // nctiles + 1
+  // updated on the device
   unsigned long long step;
-  int32_t permuted; // 1 if the last completed step reordered the particles
+  int32_t cur;
   int32_t pad_i;
 };
 
