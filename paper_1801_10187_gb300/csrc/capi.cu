@@ -136,8 +136,9 @@ struct Engine {
   // device tables
   BoxDev* d_boxes = nullptr;
   int n_records = 0;
-  int2* d_spans[4] = {nullptr, nullptr, nullptr, nullptr};  // per kernel variant
-  int n_spans[4] = {0, 0, 0, 0};
+  // per kernel variant: thermostat (1) | walls or beads (2) | warp-spread members (4)
+  int2* d_spans[8] = {};
+  int n_spans[8] = {};
   ScanSeg* d_bsegs = nullptr;
   int2* d_bstiles = nullptr;
   int n_bstiles = 0;
@@ -152,7 +153,7 @@ struct Engine {
   int* d_err = nullptr;
   double* d_partials = nullptr;
   bool any_beads = false;
-  int cells_bps[3][4] = {};
+  int cells_bps[3][8] = {};
 
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // MODE_P, MODE_F, MODE_C
   bool tables_ok = false;
@@ -171,8 +172,9 @@ struct Engine {
       own_stream = true;
     }
     for (int m = 0; m < 3; ++m)
-      for (int v = 0; v < 4; ++v) {
-        cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
+      for (int v = 0; v < 8; ++v) {
+        if (v & 4) cells_bps[m][v] = mixed ? cells_warp_blocks_per_sm((v & 1) != 0, m) : 1;
+        else cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
         if (cells_bps[m][v] < 1) cells_bps[m][v] = 1;
       }
     CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
@@ -188,11 +190,11 @@ struct Engine {
   }
 
   void free_tables() {
-    void* ptrs[] = {d_boxes, d_spans[0], d_spans[1], d_spans[2], d_spans[3], d_bsegs, d_bstiles,
-                    d_btiles, d_mdtiles, d_tsum, d_gscan, d_toff};
+    void* ptrs[] = {d_boxes, d_bsegs, d_bstiles, d_btiles, d_mdtiles, d_tsum, d_gscan, d_toff};
     for (void* q : ptrs)
       if (q) cudaFree(q);
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < 8; ++v) {
+      if (d_spans[v]) cudaFree(d_spans[v]);
       d_spans[v] = nullptr;
       n_spans[v] = 0;
     }
@@ -287,7 +289,7 @@ struct Engine {
     tables_ok = true;
     if (live.empty()) return MPCD_OK;
     std::vector<BoxDev> rec;
-    std::vector<int2> sp[4], bst, bt, mt;
+    std::vector<int2> sp[8], bst, bt, mt;
     std::vector<ScanSeg> bseg;
     any_beads = false;
     int max_cl = 1;
@@ -300,7 +302,8 @@ struct Engine {
       b->dev_index = (int)i;
       rec.push_back(b->d);
       const BoxDev& d = b->d;
-      const int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0);
+      int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0);
+      if (mixed && !(variant & 2) && d.K <= WARP_MAX_K) variant |= 4;
       for (int c0 = 0; c0 < d.ncells; c0 += BLOCK) sp[variant].push_back(make_int2((int)i, c0));
       if (d.nbead > 0) {
         any_beads = true;
@@ -322,7 +325,7 @@ struct Engine {
       return MPCD_OK;
     };
     if ((rc = up(rec, d_boxes, &n_records))) return rc;
-    for (int v = 0; v < 4; ++v)
+    for (int v = 0; v < 8; ++v)
       if ((rc = up(sp[v], d_spans[v], &n_spans[v]))) return rc;
     if ((rc = up(bseg, d_bsegs, nullptr))) return rc;
     if ((rc = up(bst, d_bstiles, &n_bstiles))) return rc;
@@ -343,9 +346,13 @@ struct Engine {
   }
 
   void launch_cells_all(int mode) {
-    for (int v = 0; v < 4; ++v)
-      launch_cells(mixed, v, mode, d_boxes, d_spans[v], n_spans[v],
-                   grid_for(n_spans[v], cells_bps[mode][v]), d_err, stream);
+    for (int v = 0; v < 8; ++v) {
+      const int grid = grid_for(n_spans[v], cells_bps[mode][v]);
+      if (v & 4)
+        launch_cells_warp((v & 1) != 0, mode, d_boxes, d_spans[v], n_spans[v], grid, d_err, stream);
+      else
+        launch_cells(mixed, v, mode, d_boxes, d_spans[v], n_spans[v], grid, d_err, stream);
+    }
   }
 
   // Solute: MD substeps and bead grouping for the step in the records.

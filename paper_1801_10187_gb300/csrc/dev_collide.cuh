@@ -9,9 +9,6 @@
 
 namespace mpcd {
 
-template <bool MIXED>
-using real_t = typename std::conditional<MIXED, float, double>::type;
-
 // ---------------------------------------------------------------------------
 // Exact conversions on the integer pipe.  On GB300 the float<->int64
 // conversion instructions share the slow FP64 pipe, so the mixed model does

@@ -15,72 +15,12 @@
 // read).  Nothing else touches the particles: no separate sort, scan or
 // reorder pass exists, and every record moves as one 32-byte sector.
 #include "dev_collide.cuh"
+#include "dev_rows.cuh"
 #include "dev_stream.cuh"
 #include "kernels.h"
 #include "mpcd_internal.cuh"
 
 namespace mpcd {
-
-template <bool MIXED>
-using rec_t = typename std::conditional<MIXED, RecF, RecD>::type;
-
-__device__ __forceinline__ void load_rec(const RecF* p, float r[3], float v[3], uint32_t& tag) {
-  const float4 a = reinterpret_cast<const float4*>(p)[0];
-  const float4 b = reinterpret_cast<const float4*>(p)[1];
-  r[0] = a.x; r[1] = a.y; r[2] = a.z;
-  v[0] = a.w; v[1] = b.x; v[2] = b.y;
-  tag = __float_as_uint(b.z);
-}
-__device__ __forceinline__ void store_rec(RecF* p, const float r[3], const float v[3], uint32_t tag) {
-  reinterpret_cast<float4*>(p)[0] = make_float4(r[0], r[1], r[2], v[0]);
-  reinterpret_cast<float4*>(p)[1] = make_float4(v[1], v[2], __uint_as_float(tag), 0.0f);
-}
-__device__ __forceinline__ void load_rec(const RecD* p, double r[3], double v[3], uint32_t& tag) {
-  const double2 a = reinterpret_cast<const double2*>(p)[0];
-  const double2 b = reinterpret_cast<const double2*>(p)[1];
-  const double2 c = reinterpret_cast<const double2*>(p)[2];
-  const uint4 d = reinterpret_cast<const uint4*>(p)[3];
-  r[0] = a.x; r[1] = a.y; r[2] = b.x;
-  v[0] = b.y; v[1] = c.x; v[2] = c.y;
-  tag = d.x;
-}
-__device__ __forceinline__ void store_rec(RecD* p, const double r[3], const double v[3], uint32_t tag) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(r[0], r[1]);
-  reinterpret_cast<double2*>(p)[1] = make_double2(r[2], v[0]);
-  reinterpret_cast<double2*>(p)[2] = make_double2(v[1], v[2]);
-  reinterpret_cast<uint4*>(p)[3] = make_uint4(tag, 0u, 0u, 0u);
-}
-__device__ __forceinline__ void load_v(const RecF* p, float v[3]) {
-  const float4 a = reinterpret_cast<const float4*>(p)[0];
-  const float2 b = reinterpret_cast<const float2*>(p)[2];
-  v[0] = a.w; v[1] = b.x; v[2] = b.y;
-}
-__device__ __forceinline__ void load_v(const RecD* p, double v[3]) {
-  const double2 b = reinterpret_cast<const double2*>(p)[1];
-  const double2 c = reinterpret_cast<const double2*>(p)[2];
-  v[0] = b.y; v[1] = c.x; v[2] = c.y;
-}
-
-// Append a record to the row of cell c in the output set (or to the output
-// overflow list when the row is full).
-template <bool MIXED>
-__device__ __forceinline__ void insert(const BoxDev& B, int out, uint32_t c,
-                                       const real_t<MIXED> r[3], const real_t<MIXED> v[3],
-                                       uint32_t tag, int* err) {
-  using R = rec_t<MIXED>;
-  const uint32_t slot = atomicAdd(&B.cnt[out][c], 1u);
-  if (slot < (uint32_t)B.K) {
-    store_rec(((R*)B.rows[out]) + (size_t)c * B.K + slot, r, v, tag);
-  } else {
-    const uint32_t j = atomicAdd(&B.ovf_n[out], 1u);
-    if (j < (uint32_t)B.ovf_cap) {
-      store_rec(((R*)B.ovf_rec[out]) + j, r, v, tag);
-      B.ovf_cell[out][j] = c;
-    } else {
-      atomicOr(err, ERR_OVERFLOW_CAP);
-    }
-  }
-}
 
 template <bool MIXED, bool THERMO, bool EXTRA, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxes,
@@ -115,7 +55,7 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
     R* row = ((R*)B.rows[cur]) + (size_t)cell * K;
     R* ovf = (R*)B.ovf_rec[cur];
     const uint32_t* ovf_cell = B.ovf_cell[cur];
-    const uint32_t novf = has_ovf ? B.ovf_n[cur] : 0u;
+    const uint32_t novf = has_ovf ? min(B.ovf_n[cur], (uint32_t)B.ovf_cap) : 0u;
     int b0 = 0, nbt = 0;
     if (EXTRA && MODE != MODE_P && B.nbead > 0) {
       const int g = cell / B.tc;
@@ -261,7 +201,7 @@ __global__ void k_extract(const BoxDev* __restrict__ box, real_t<MIXED>* __restr
       if (cell_out) cell_out[tag] = cell;
     }
   }
-  const uint32_t novf = B.ovf_n[cur];
+  const uint32_t novf = min(B.ovf_n[cur], (uint32_t)B.ovf_cap);
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < novf; j += stride) {
     T r[3], v[3];
     uint32_t tag;

@@ -9,9 +9,6 @@
 
 namespace mpcd {
 
-template <bool MIXED>
-using real_t = typename std::conditional<MIXED, float, double>::type;
-
 // Per-particle pass: block partial sums of P and KE (double, fixed block
 // decomposition) and fixed-point sums per cell of the unshifted grid.
 template <bool MIXED>

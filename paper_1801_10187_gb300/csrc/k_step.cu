@@ -12,9 +12,6 @@
 
 namespace mpcd {
 
-template <bool MIXED>
-using real_t = typename std::conditional<MIXED, float, double>::type;
-
 // ---------------------------------------------------------------------------
 // Solute: velocity-Verlet substeps with harmonic bonds along each chain, then
 // binning of the beads with the step's shift.  One block holds whole chains

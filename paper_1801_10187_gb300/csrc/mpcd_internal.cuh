@@ -12,9 +12,15 @@
 // own arrays, grouped per tile of 32 cells.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace mpcd {
+
+// Storage and arithmetic type of the two precision models: FP64, or the mixed
+// model's FP32 particles.
+template <bool MIXED>
+using real_t = typename std::conditional<MIXED, float, double>::type;
 
 // Random-stream purposes XORed into the high key word.
 constexpr uint32_t PURPOSE_SHIFT = 0x53484654u;

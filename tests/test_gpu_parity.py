@@ -299,3 +299,50 @@ def test_profile_matches_oracle(precision):
     ref = oracle.profile(oracle.Params(n=n), oracle.State(pos, vel), 24)
     assert np.allclose(prof, ref, rtol=0, atol=1e-12)
     assert prof[12] > 0.0  # the body force drives +x flow in the middle of the channel
+
+
+@pytest.mark.parametrize("thermostat", [False, True])
+def test_mixed_dense_box_many_steps(thermostat):
+    """20^3 cells at 12 per cell (rows of 40 records, several member windows
+    per warp), 12 steps: bit-exact against the mixed oracle."""
+    pos, vel, st, cells, counts, ref, (rc, rk) = run_pair((20, 20, 20), 12, "mixed", steps=12,
+                                                          seed=31, thermostat=thermostat)
+    assert st == 12
+    np.testing.assert_array_equal(cells, rc)
+    np.testing.assert_array_equal(counts, rk)
+    np.testing.assert_array_equal(pos, ref.pos)
+    np.testing.assert_array_equal(vel, ref.vel)
+
+
+def test_mixed_large_velocities_exact():
+    """Members with |v| >= 1024 leave the int32 split of the fixed-point sums
+    and take the exact int64 path: results stay bit-exact."""
+    n = (6, 6, 6)
+    s = inputs.solvent(n, 5, seed=12, mixed=True)
+    vel = s.vel.copy()
+    rng = np.random.default_rng(0)
+    idx = rng.choice(len(vel), 40, replace=False)
+    vel[idx] = rng.uniform(1024.0, 1500.0, (40, 3)) * rng.choice([-1.0, 1.0], (40, 3))
+    vel = vel.astype(np.float32).astype(np.float64)
+    for thermostat in (False, True):
+        box = pkg.Box(n=n, seed=12, precision="mixed", thermostat=thermostat)
+        box.set_state(s.pos, vel)
+        box.step(2)
+        pos, v, _, _, _ = box.get_state()
+        box.close()
+        ref = oracle.State(s.pos.copy(), vel.copy())
+        oracle.step(oracle.Params(n=n, seed=12, thermostat=thermostat, precision=oracle.MIXED), ref, 2)
+        np.testing.assert_array_equal(pos, ref.pos)
+        np.testing.assert_array_equal(v, ref.vel)
+
+
+@pytest.mark.parametrize("rho", [320, 340])
+def test_mixed_row_capacity_limits(rho):
+    """Rows of 432 records (the largest the warp-spread kernel takes) and of
+    456 (handled by the per-cell kernel): both bit-exact."""
+    pos, vel, st, cells, counts, ref, (rc, rk) = run_pair((3, 3, 3), rho, "mixed", steps=3,
+                                                          seed=40, thermostat=True)
+    np.testing.assert_array_equal(cells, rc)
+    np.testing.assert_array_equal(counts, rk)
+    np.testing.assert_array_equal(pos, ref.pos)
+    np.testing.assert_array_equal(vel, ref.vel)
