@@ -136,7 +136,8 @@ struct Engine {
   // device tables
   BoxDev* d_boxes = nullptr;
   int n_records = 0;
-  // per kernel variant: thermostat (1) | walls or beads (2) | warp-spread members (4)
+  // per kernel variant: thermostat (1) | walls or beads (2) | warp-spread members (4);
+  // for the warp-spread kernel bit 2 means a nonzero body force instead
   int2* d_spans[8] = {};
   int n_spans[8] = {};
   ScanSeg* d_bsegs = nullptr;
@@ -173,7 +174,7 @@ struct Engine {
     }
     for (int m = 0; m < 3; ++m)
       for (int v = 0; v < 8; ++v) {
-        if (v & 4) cells_bps[m][v] = mixed ? cells_warp_blocks_per_sm((v & 1) != 0, m) : 1;
+        if (v & 4) cells_bps[m][v] = mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, m) : 1;
         else cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
         if (cells_bps[m][v] < 1) cells_bps[m][v] = 1;
       }
@@ -303,7 +304,11 @@ struct Engine {
       rec.push_back(b->d);
       const BoxDev& d = b->d;
       int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0);
-      if (mixed && !(variant & 2) && d.K <= WARP_MAX_K) variant |= 4;
+      if (mixed && !(variant & 2) && d.K <= WARP_MAX_K &&
+          std::max(d.n[0], std::max(d.n[1], d.n[2])) < (1 << 22)) {
+        const bool force = d.g[0] != 0.0 || d.g[1] != 0.0 || d.g[2] != 0.0;
+        variant = 4 | (d.thermostat ? 1 : 0) | (force ? 2 : 0);
+      }
       for (int c0 = 0; c0 < d.ncells; c0 += BLOCK) sp[variant].push_back(make_int2((int)i, c0));
       if (d.nbead > 0) {
         any_beads = true;
@@ -349,7 +354,8 @@ struct Engine {
     for (int v = 0; v < 8; ++v) {
       const int grid = grid_for(n_spans[v], cells_bps[mode][v]);
       if (v & 4)
-        launch_cells_warp((v & 1) != 0, mode, d_boxes, d_spans[v], n_spans[v], grid, d_err, stream);
+        launch_cells_warp((v & 1) != 0, (v & 2) != 0, mode, d_boxes, d_spans[v], n_spans[v], grid,
+                          d_err, stream);
       else
         launch_cells(mixed, v, mode, d_boxes, d_spans[v], n_spans[v], grid, d_err, stream);
     }

@@ -80,6 +80,17 @@ __device__ __forceinline__ float i64_to_float(long long q) {
   return __uint_as_float(sign | ((uint32_t)(e + 127) << 23) | ((uint32_t)m & 0x7FFFFFu));
 }
 
+// Correctly rounded floats of 32-bit words: the word itself, 2^32 minus the
+// word, and twice the word minus 2^32 (the last two as an exact power-of-two
+// scaling of a 32-bit value); they equal i64_to_float of the same integers.
+__device__ __forceinline__ float word_to_float(uint32_t w) { return __uint2float_rn(w); }
+__device__ __forceinline__ float comp_word_to_float(uint32_t w) {
+  return w == 0u ? 4294967296.0f : __uint2float_rn(0u - w);
+}
+__device__ __forceinline__ float centred_word_half_to_float(uint32_t w) {
+  return __int2float_rn((int)(w ^ 0x80000000u));  // w - 2^31
+}
+
 // Exact float of 0 <= n < 2^23 on the FMA pipe (2^23 + n has n as mantissa).
 __device__ __forceinline__ float small_to_float(int n) {
   if ((unsigned)n < (1u << 23)) return __int_as_float(0x4B000000 | n) - 8388608.0f;
@@ -108,19 +119,14 @@ __device__ __forceinline__ void turn_cos_sin(uint32_t w, float& c, float& s) {
   const uint32_t f = w & 0x1FFFFFFFu;
   const uint32_t g = (o & 1u) ? (0x20000000u - f) : f;
   const float quarter_pi = (float)(3.14159265358979323846 / 4.0);
-  const float x = (i64_to_float((long long)g) * 0x1p-29f) * quarter_pi;
+  const float x = (word_to_float(g) * 0x1p-29f) * quarter_pi;
   float sb, cb;
   series_sincos(x, sb, cb);
-  switch (o) {
-    case 0: c = cb; s = sb; break;
-    case 1: c = sb; s = cb; break;
-    case 2: c = -sb; s = cb; break;
-    case 3: c = -cb; s = sb; break;
-    case 4: c = -cb; s = -sb; break;
-    case 5: c = -sb; s = -cb; break;
-    case 6: c = sb; s = -cb; break;
-    default: c = cb; s = -sb; break;
-  }
+  // octants 1, 2, 5, 6 swap the two; cos is negative in octants 2..5, sin in 4..7
+  const bool swap = ((o + 1u) >> 1) & 1u;
+  const uint32_t cneg = (((o + 2u) >> 2) & 1u) << 31, sneg = ((o >> 2) & 1u) << 31;
+  c = __uint_as_float(__float_as_uint(swap ? sb : cb) ^ cneg);
+  s = __uint_as_float(__float_as_uint(swap ? cb : sb) ^ sneg);
 }
 
 __device__ __forceinline__ float series_log(float x) {
@@ -151,9 +157,9 @@ __device__ __forceinline__ float series_log(float x) {
 __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, uint32_t cell,
                                         float n[3]) {
   const uint4 w = draw(B, PURPOSE_ROT, cell, 0u, t);
-  const float a = i64_to_float((long long)w.x) * 0x1p-32f;
-  const float b = i64_to_float(4294967296LL - (long long)w.x) * 0x1p-32f;
-  const float z = i64_to_float(2LL * (long long)w.x - 4294967296LL) * 0x1p-32f;
+  const float a = word_to_float(w.x) * 0x1p-32f;
+  const float b = comp_word_to_float(w.x) * 0x1p-32f;
+  const float z = centred_word_half_to_float(w.x) * 0x1p-31f;
   const float r = 2.0f * sqrtf(a * b);
   float c, s;
   turn_cos_sin(w.y, c, s);
@@ -190,8 +196,8 @@ __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_
   for (uint32_t j = 0; j < 64u; ++j) {
     const uint4 wa = draw(B, PURPOSE_THERMO, cell, 1u + 2u * j, t);
     const uint4 wb = draw(B, PURPOSE_THERMO, cell, 2u + 2u * j, t);
-    const float e1 = i64_to_float(4294967296LL - (long long)wa.x) * 0x1p-32f;
-    const float U3 = i64_to_float((long long)wb.x) * 0x1p-32f;
+    const float e1 = comp_word_to_float(wa.x) * 0x1p-32f;
+    const float U3 = word_to_float(wb.x) * 0x1p-32f;
     float c2, s2;
     turn_cos_sin(wa.z, c2, s2);
     const float x = sqrtf(-2.0f * series_log(e1)) * c2;

@@ -17,8 +17,10 @@
 //            about u, the factor xi) and leaves them in shared memory
 //   pass 2   each member collides with its cell's parameters, streams, is
 //            binned under the next shift and appended to its new row
-// Members beyond the row capacity (overflow list) stay with the lane of their
-// cell, as in k_cells.  The int32 parts stay in range while K <= 448 and
+// The parameters a member needs (time step, box, rotation, the thresholds of
+// the next grid shift, row pointers) are staged once per span in shared
+// memory.  Members beyond the row capacity (overflow list) stay with the lane
+// of their cell, as in k_cells.  The int32 parts stay in range while K <= 448 and
 // |v| < 1024; larger velocities take an exact int64 path through shared memory.
 #include "dev_collide.cuh"
 #include "dev_rows.cuh"
@@ -33,13 +35,24 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int WARPS = BLOCK / 32;
 
+constexpr int MAP_MEMBERS = 1024;
+
 struct WarpShared {
   int h[3][32];          // sum over the cell of H (momentum); h[0] reused for the energy
   int l[3][32];          // sum of L
   long long x[4][32];    // exact int64 sums of out-of-range members (momentum, energy)
   float4 prm[2][32];     // (u, xi), (axis, 0) per cell
   unsigned char own[32]; // lane of the cell whose first member sits at each window slot
+  unsigned char map[MAP_MEMBERS];  // owner lane of each member
 };
+
+// rne(Q) as a float for Q = sh 2^20 + sl + x: one rounding of an exact sum of
+// two exact floats when the parts are small (always, for real velocities).
+__device__ __forceinline__ float split_sum_to_float(int sh, int sl, long long x) {
+  if (x == 0 && sh > -16777216 && sh < 16777216 && sl > -16777216 && sl < 16777216)
+    return __fadd_rn(__int2float_rn(sh) * 1048576.0f, __int2float_rn(sl));
+  return i64_to_float((long long)sh * 1048576LL + (long long)sl + x);
+}
 
 __device__ __forceinline__ void add_split(float v, int& H, int& L, long long* slow) {
   if (!split32(v, H, L)) {
@@ -49,30 +62,96 @@ __device__ __forceinline__ void add_split(float v, int& H, int& L, long long* sl
   }
 }
 
+// Per-span parameters shared by the block.
+struct SpanParams {
+  float dt, ca, sa, omc, m;
+  float L[3], hg[3], gdt[3];
+  float lo[3], hi[3];  // binning thresholds of the next grid shift (see bin_axis)
+  int n[3], K;
+  RecF* rows_cur;
+  RecF* rows_out;
+  uint32_t* cnt_out;
+  RecF* ovf_out;
+  uint32_t* ovf_cell_out;
+  uint32_t* ovf_n_out;
+  int ovf_cap, pad;
+};
+
+// floor(x - s) for 0 <= x < 2^22 and s = S 2^-32 in [-1/2, 1/2), exactly:
+// x = i0 + f with i0 = floor(x) (round-down add of 2^23) and f exact; then
+// floor(x - s) = i0 - [f < s] + [f >= 1 + s].  f is a float, so f < s is
+// f < lo with lo = RN(s), or its successor when RN(s) < s; f >= 1 + s is
+// f >= hi with hi = RN(1 + s), or its successor when RN(1 + s) < 1 + s.
+__device__ __forceinline__ void bin_thresholds(long long S, float& lo, float& hi) {
+  const double s = (double)S * 0x1p-32;
+  const float sh = (float)s;
+  lo = ((double)sh < s) ? nextafterf(sh, INFINITY) : sh;
+  const double t = 1.0 + s;
+  const float th = (float)t;
+  hi = ((double)th < t) ? nextafterf(th, INFINITY) : th;
+}
+
+__device__ __forceinline__ int bin_axis(float x, float lo, float hi, int n) {
+  const float t = __fadd_rd(x, 8388608.0f);
+  const int i0 = __float_as_int(t) - 0x4B000000;
+  const float f = __fsub_rn(x, __fsub_rn(t, 8388608.0f));
+  int i = i0 - (f < lo ? 1 : 0) + (f >= hi ? 1 : 0);
+  if (i < 0) i += n;
+  if (i >= n) i -= n;
+  return i;
+}
+
+__device__ __forceinline__ float wrap_fast(float x, float L) {
+  if (x >= L) x -= L;
+  else if (x < 0.0f) x += L;
+  return x;
+}
+
 }  // namespace
 
-template <bool THERMO, int MODE>
+template <bool THERMO, int MODE, bool FORCE>
 __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restrict__ boxes,
                                                          const int2* __restrict__ spans,
                                                          int nspans, int* err) {
   using R = RecF;
   __shared__ WarpShared shw[WARPS];
-  __shared__ long long sSn[3];
+  __shared__ SpanParams sp_;
   const int lane = threadIdx.x & 31;
   WarpShared& W = shw[threadIdx.x >> 5];
+  const SpanParams& H = sp_;
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
     const int2 tt = spans[sp];
     const BoxDev& B = boxes[tt.x];
     const unsigned long long t = B.step;
     __syncthreads();
-    if (threadIdx.x == 0 && MODE != MODE_C) shift_units(B, MODE == MODE_P ? t : t + 1ull, sSn);
+    if (threadIdx.x == 0) {
+      SpanParams& P = sp_;
+      P.dt = B.dt_f; P.ca = B.ca_f; P.sa = B.sa_f; P.omc = B.omc_f; P.m = B.m_f;
+      for (int q = 0; q < 3; ++q) {
+        P.L[q] = B.L_f[q]; P.hg[q] = B.hg_f[q]; P.gdt[q] = B.gdt_f[q]; P.n[q] = B.n[q];
+      }
+      P.K = B.K;
+      const int out = B.cur ^ 1;
+      P.rows_cur = (RecF*)B.rows[B.cur];
+      P.rows_out = (RecF*)B.rows[out];
+      P.cnt_out = B.cnt[out];
+      P.ovf_out = (RecF*)B.ovf_rec[out];
+      P.ovf_cell_out = B.ovf_cell[out];
+      P.ovf_n_out = &B.ovf_n[out];
+      P.ovf_cap = B.ovf_cap;
+      if (MODE != MODE_C) {
+        long long S[3];
+        shift_units(B, MODE == MODE_P ? t : t + 1ull, S);
+        for (int q = 0; q < 3; ++q) bin_thresholds(S[q], P.lo[q], P.hi[q]);
+      }
+    }
     __syncthreads();
     const int c0 = tt.y + (int)(threadIdx.x & ~31u);
     if (c0 >= B.ncells) continue;  // warp-uniform
     const int cell = c0 + lane;
     const bool valid = cell < B.ncells;
-    const int cur = B.cur, out = cur ^ 1;
-    const int K = B.K;
+    const int cur = B.cur;
+    const int K = H.K;
     const uint32_t n = valid ? B.cnt[cur][cell] : 0u;
     if (MODE != MODE_C && n) B.cnt[cur][cell] = 0u;  // this set is written two steps on
     const int nrow = (int)n < K ? (int)n : K;
@@ -85,36 +164,41 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
     }
     const int off = incl - nrow;
     const int N = __shfl_sync(FULL, incl, 31);
-    R* rows = ((R*)B.rows[cur]) + (size_t)c0 * K;
+    R* rows = H.rows_cur + (size_t)c0 * K;
     const R* ovf = (const R*)B.ovf_rec[cur];
     const uint32_t* ovf_cell = B.ovf_cell[cur];
     const uint32_t novf =
         __any_sync(FULL, has_ovf) ? min(B.ovf_n[cur], (uint32_t)B.ovf_cap) : 0u;
 
-    // Visit the row members in windows of 32: f(o, k, act, seg, head) gets the
-    // owning lane o, the slot k in its row, whether the lane holds a member,
-    // the mask of the lanes of the same cell in this window and whether this
-    // lane is the first of them.
-    auto members = [&](auto&& f) {
-      int carry = 0;
-      for (int base = 0; base < N; base += 32) {
-        const int rel = off - base;
-        const bool st = nrow > 0 && rel >= 0 && rel < 32;
-        if (st) W.own[rel] = (unsigned char)lane;
-        const unsigned sb = __reduce_or_sync(FULL, st ? (1u << rel) : 0u);
-        __syncwarp();
-        const unsigned upto = FULL >> (31 - lane);  // bits 0 .. lane
-        const unsigned le = sb & upto;
-        const int lo = le ? 31 - __clz(le) : 0;
-        const int o = le ? (int)W.own[lo] : carry;
-        const unsigned gt = sb & ~upto;
-        const int hi = gt ? __ffs(gt) - 2 : 31;
-        const unsigned seg = ((2u << hi) - 1u) & ~((1u << lo) - 1u);
-        const int k = base + lane - __shfl_sync(FULL, off, o);
-        f(o, k, base + lane < N, seg, lane == lo);
-        carry = __shfl_sync(FULL, o, 31);
-        __syncwarp();
-      }
+    // Owner lane of every member: a byte map for up to MAP_MEMBERS members,
+    // else found per window of 32 (own[] holds the lanes whose first member
+    // falls in the window).
+    const bool mapped = N <= MAP_MEMBERS;
+    if (mapped)
+      for (int j = 0; j < nrow; ++j) W.map[off + j] = (unsigned char)lane;
+    __syncwarp();
+    int carry = 0;
+    auto owner = [&](int base) -> int {  // warp-collective
+      if (mapped) return W.map[min(base + lane, N - 1)];
+      const int rel = off - base;
+      const bool st = nrow > 0 && rel >= 0 && rel < 32;
+      if (st) W.own[rel] = (unsigned char)lane;
+      const unsigned sb = __reduce_or_sync(FULL, st ? (1u << rel) : 0u);
+      __syncwarp();
+      const unsigned le = sb & (FULL >> (31 - lane));
+      const int o = le ? (int)W.own[31 - __clz(le)] : carry;
+      carry = __shfl_sync(FULL, o, 31);
+      __syncwarp();
+      return o;
+    };
+    // lanes of the same cell as this one within a window: from the heads
+    auto segment = [&](bool head) -> unsigned {
+      const unsigned hm = __ballot_sync(FULL, head || lane == 0);
+      const unsigned upto = FULL >> (31 - lane);
+      const int lo = 31 - __clz(hm & upto);
+      const unsigned gt = hm & ~upto;
+      const int hi = gt ? __ffs(gt) - 2 : 31;
+      return ((2u << hi) - 1u) & ~((1u << lo) - 1u);
     };
 
     if (MODE != MODE_P) {
@@ -127,53 +211,63 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
       }
       W.x[3][lane] = 0;
       __syncwarp();
-      members([&](int o, int k, bool act, unsigned seg, bool head) {
-        int H[3] = {0, 0, 0}, L[3] = {0, 0, 0};
+      for (int base = 0; base < N; base += 32) {
+        const int o = owner(base);
+        const int k = base + lane - __shfl_sync(FULL, off, o);
+        const bool act = base + lane < N;
+        int Hs[3] = {0, 0, 0}, Ls[3] = {0, 0, 0};
         if (act) {
           const float* p = reinterpret_cast<const float*>(rows + (size_t)o * K + k);
           const float v0 = p[3];
           const float2 v12 = *reinterpret_cast<const float2*>(p + 4);
-          add_split(v0, H[0], L[0], &W.x[0][o]);
-          add_split(v12.x, H[1], L[1], &W.x[1][o]);
-          add_split(v12.y, H[2], L[2], &W.x[2][o]);
+          add_split(v0, Hs[0], Ls[0], &W.x[0][o]);
+          add_split(v12.x, Hs[1], Ls[1], &W.x[1][o]);
+          add_split(v12.y, Hs[2], Ls[2], &W.x[2][o]);
         }
+        const bool head = act && k == 0;
+        const unsigned seg = segment(head);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          const int sh = __reduce_add_sync(seg, H[q]);
-          const int sl = __reduce_add_sync(seg, L[q]);
-          if (head) {
+          const int sh = __reduce_add_sync(seg, Hs[q]);
+          const int sl = __reduce_add_sync(seg, Ls[q]);
+          if (head || lane == 0) {
             W.h[q][o] += sh;
             W.l[q][o] += sl;
           }
         }
-      });
-      __syncwarp();
+        __syncwarp();
+      }
 
-      // ---- per cell: u, then (thermostat) the energy about u, axis, xi ----
-      CellAcc<true> a;
+      // ---- per cell: u (Sec. 3.5), then the energy about u, axis and xi ----
       float u[3] = {0.0f, 0.0f, 0.0f};
+      long long ovq[3] = {0, 0, 0};
+      if (has_ovf)
+        for (uint32_t j = 0; j < novf; ++j)
+          if (ovf_cell[j] == (uint32_t)cell) {
+            float w[3];
+            load_v(ovf + j, w);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) ovq[q] += fix32_rne(w[q]);
+          }
       if (n > 0) {
+        const float M = H.m * small_to_float((int)n);
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-          a.q[q] = (long long)W.h[q][lane] * 1048576LL + (long long)W.l[q][lane] + W.x[q][lane];
-        if (has_ovf)
-          for (uint32_t j = 0; j < novf; ++j)
-            if (ovf_cell[j] == (uint32_t)cell) {
-              float w[3];
-              load_v(ovf + j, w);
-#pragma unroll
-              for (int q = 0; q < 3; ++q) a.q[q] += fix32_rne(w[q]);
-            }
-        a.ns = (int)n;
-        a.mean_velocity(B, u, false);
+        for (int q = 0; q < 3; ++q) {
+          const float P = H.m * split_sum_to_float(W.h[q][lane], W.l[q][lane], W.x[q][lane] + ovq[q]);
+          u[q] = (P * 0x1p-32f) / M;
+        }
         W.prm[0][lane] = make_float4(u[0], u[1], u[2], 1.0f);
       }
+      float xi = 1.0f;
       if (THERMO) {
         W.h[0][lane] = 0;
         W.l[0][lane] = 0;
         __syncwarp();
-        members([&](int o, int k, bool act, unsigned seg, bool head) {
-          int H = 0, L = 0;
+        for (int base = 0; base < N; base += 32) {
+          const int o = owner(base);
+          const int k = base + lane - __shfl_sync(FULL, off, o);
+          const bool act = base + lane < N;
+          int He = 0, Le = 0;
           if (act) {
             const float* p = reinterpret_cast<const float*>(rows + (size_t)o * K + k);
             const float v0 = p[3];
@@ -181,93 +275,161 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
             const float4 uo = W.prm[0][o];
             const float d0 = v0 - uo.x, d1 = v12.x - uo.y, d2 = v12.y - uo.z;
             const float e = d0 * d0 + d1 * d1 + d2 * d2;
-            add_split(e, H, L, &W.x[3][o]);
+            add_split(e, He, Le, &W.x[3][o]);
           }
-          const int sh = __reduce_add_sync(seg, H);
-          const int sl = __reduce_add_sync(seg, L);
-          if (head) {
+          const bool head = act && k == 0;
+          const unsigned seg = segment(head);
+          const int sh = __reduce_add_sync(seg, He);
+          const int sl = __reduce_add_sync(seg, Le);
+          if (head || lane == 0) {
             W.h[0][o] += sh;
             W.l[0][o] += sl;
           }
-        });
-        __syncwarp();
+          __syncwarp();
+        }
         if (n > 0) {
-          a.es = (long long)W.h[0][lane] * 1048576LL + (long long)W.l[0][lane] + W.x[3][lane];
+          long long ove = 0;
           if (has_ovf)
             for (uint32_t j = 0; j < novf; ++j)
               if (ovf_cell[j] == (uint32_t)cell) {
                 float w[3];
                 load_v(ovf + j, w);
-                a.add_solvent_energy(B, w, u);
+                const float d0 = w[0] - u[0], d1 = w[1] - u[1], d2 = w[2] - u[2];
+                ove += fix32_rne(d0 * d0 + d1 * d1 + d2 * d2);
               }
+          // Eq. thermo: E_k about u, E^ ~ Gamma(3(n-1)/2, kT), xi = sqrt(E^/E_k)
+          const float E = H.m * split_sum_to_float(W.h[0][lane], W.l[0][lane], W.x[3][lane] + ove);
+          const float Ek = (0.5f * E) * 0x1p-32f;
+          if (n >= 2 && Ek > 0.0f) {
+            float ehat;
+            if (gamma_draw(B, t, (uint32_t)cell, (int)n, ehat)) xi = sqrtf(ehat / Ek);
+            else atomicOr(err, ERR_GAMMA_CAP);
+          }
         }
       }
-      CellParams<float> prm;
       if (n > 0) {
-        auto no_beads = [](int, int&) { return false; };
-        cell_finish<true>(B, t, (uint32_t)cell, a, u, 0, no_beads, THERMO, false, prm, err);
-        W.prm[0][lane] = make_float4(prm.u[0], prm.u[1], prm.u[2], prm.xi);
-        W.prm[1][lane] = make_float4(prm.n[0], prm.n[1], prm.n[2], 0.0f);
+        float ax[3];
+        axis_of(B, t, (uint32_t)cell, ax);  // Sec. 3.6
+        W.prm[0][lane] = make_float4(u[0], u[1], u[2], xi);
+        W.prm[1][lane] = make_float4(ax[0], ax[1], ax[2], 0.0f);
       }
       __syncwarp();
     }
 
     // ---- pass 2: collide (Eq. srd), stream (Eq. stream), bin (Sec. 3.4) ----
-    auto process = [&](R* p, const CellParams<float>& prm) {
-      float r[3], w[3];
-      uint32_t tag;
-      load_rec(p, r, w, tag);
-      if (MODE != MODE_P) collide_one<true>(B, prm, w, THERMO);
+    auto finish = [&](R* p, float r[3], float w[3], uint32_t tag, int o) {
+      if (MODE != MODE_P) {
+        const float4 pa = W.prm[0][o], pb = W.prm[1][o];
+        const float nn[3] = {pb.x, pb.y, pb.z};
+        const float uu[3] = {pa.x, pa.y, pa.z};
+        float d[3], rr[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) d[q] = w[q] - uu[q];
+        rotate(nn, H.ca, H.sa, H.omc, d, rr);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) w[q] = uu[q] + (THERMO ? pa.w * rr[q] : rr[q]);
+      }
       if (MODE == MODE_C) {
         store_rec(p, r, w, tag);
         return;
       }
-      stream_one(B, r, w);
-      const uint32_t c2 = cell_of(B, sSn, r, err);
-      insert<true>(B, out, c2, r, w, tag, err);
-    };
-    auto params_of = [&](int o) {
-      CellParams<float> prm;
-      if (MODE != MODE_P) {
-        const float4 a = W.prm[0][o], b = W.prm[1][o];
-        prm.u[0] = a.x; prm.u[1] = a.y; prm.u[2] = a.z; prm.xi = a.w;
-        prm.n[0] = b.x; prm.n[1] = b.y; prm.n[2] = b.z;
+      // periodic box; the additions of zero keep the operation sequence of
+      // the general form (they turn -0 into +0)
+      bool bad = false;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (FORCE) {
+          r[q] = fmaf(w[q], H.dt, r[q]) + H.hg[q];
+          w[q] = w[q] + H.gdt[q];
+        } else {
+          r[q] = fmaf(w[q], H.dt, r[q]) + 0.0f;
+          w[q] = w[q] + 0.0f;
+        }
+        r[q] = wrap_fast(r[q], H.L[q]);
+        bad |= !(r[q] >= 0.0f && r[q] < H.L[q]);
       }
-      return prm;
+      if (bad) {  // more than one box length out, or non-finite
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (!(r[q] >= 0.0f && r[q] < H.L[q])) {
+            r[q] = r[q] - H.L[q] * floorf(r[q] / H.L[q]);
+            if (!(r[q] >= 0.0f && r[q] < H.L[q])) r[q] = 0.0f;
+          }
+      }
+      const int cx = bin_axis(r[0], H.lo[0], H.hi[0], H.n[0]);
+      const int cy = bin_axis(r[1], H.lo[1], H.hi[1], H.n[1]);
+      const int cz = bin_axis(r[2], H.lo[2], H.hi[2], H.n[2]);
+      const uint32_t c2 = (uint32_t)(cx + H.n[0] * (cy + H.n[1] * cz));
+      const uint32_t slot = atomicAdd(&H.cnt_out[c2], 1u);
+      if (slot < (uint32_t)H.K) {
+        store_rec(H.rows_out + (size_t)c2 * H.K + slot, r, w, tag);
+      } else {
+        const uint32_t j = atomicAdd(H.ovf_n_out, 1u);
+        if (j < (uint32_t)H.ovf_cap) {
+          store_rec(H.ovf_out + j, r, w, tag);
+          H.ovf_cell_out[j] = c2;
+        } else {
+          atomicOr(err, ERR_OVERFLOW_CAP);
+        }
+      }
     };
-    members([&](int o, int k, bool act, unsigned, bool) {
-      if (act) process(rows + (size_t)o * K + k, params_of(o));
-    });
+    // two windows per iteration: both records are in flight together
+    for (int base = 0; base < N; base += 64) {
+      const int oa = owner(base);
+      const int ob = base + 32 < N ? owner(base + 32) : 0;
+      const int ka = base + lane - __shfl_sync(FULL, off, oa);
+      const int kb = base + 32 + lane - __shfl_sync(FULL, off, ob);
+      const bool acta = base + lane < N, actb = base + 32 + lane < N;
+      float ra[3], wa[3], rb[3], wb[3];
+      uint32_t taga = 0u, tagb = 0u;
+      R* pa = rows + (size_t)oa * K + ka;
+      R* pb = rows + (size_t)ob * K + kb;
+      if (acta) load_rec(pa, ra, wa, taga);
+      if (actb) load_rec(pb, rb, wb, tagb);
+      if (acta) finish(pa, ra, wa, taga, oa);
+      if (actb) finish(pb, rb, wb, tagb, ob);
+    }
     if (has_ovf) {
-      const CellParams<float> prm = params_of(lane);
       for (uint32_t j = 0; j < novf; ++j)
-        if (ovf_cell[j] == (uint32_t)cell) process(((R*)B.ovf_rec[cur]) + j, prm);
+        if (ovf_cell[j] == (uint32_t)cell) {
+          R* p = ((R*)B.ovf_rec[cur]) + j;
+          float r[3], w[3];
+          uint32_t tag;
+          load_rec(p, r, w, tag);
+          finish(p, r, w, tag, lane);
+        }
     }
   }
 }
 
-template <bool TH, int MODE>
+template <bool TH, int MODE, bool FO>
 static void* warp_fn() {
-  return (void*)k_cells_warp<TH, MODE>;
+  return (void*)k_cells_warp<TH, MODE, FO>;
 }
 
-static void* warp_variant(bool thermo, int mode) {
-  if (mode == MODE_P) return thermo ? warp_fn<true, MODE_P>() : warp_fn<false, MODE_P>();
-  if (mode == MODE_F) return thermo ? warp_fn<true, MODE_F>() : warp_fn<false, MODE_F>();
-  return thermo ? warp_fn<true, MODE_C>() : warp_fn<false, MODE_C>();
+template <int MODE>
+static void* warp_variant_mode(bool thermo, bool force) {
+  if (thermo) return force ? warp_fn<true, MODE, true>() : warp_fn<true, MODE, false>();
+  return force ? warp_fn<false, MODE, true>() : warp_fn<false, MODE, false>();
 }
 
-int cells_warp_blocks_per_sm(bool thermo, int mode) {
+static void* warp_variant(bool thermo, bool force, int mode) {
+  if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force);
+  if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force);
+  return warp_variant_mode<MODE_C>(thermo, force);
+}
+
+int cells_warp_blocks_per_sm(bool thermo, bool force, int mode) {
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, warp_variant(thermo, mode), BLOCK, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, warp_variant(thermo, force, mode), BLOCK, 0);
   return nb;
 }
 
-void launch_cells_warp(bool thermo, int mode, const BoxDev* boxes, const int2* spans, int nspans,
-                       int grid, int* err, cudaStream_t s) {
+void launch_cells_warp(bool thermo, bool force, int mode, const BoxDev* boxes, const int2* spans,
+                       int nspans, int grid, int* err, cudaStream_t s) {
   if (nspans <= 0) return;
   void* args[] = {(void*)&boxes, (void*)&spans, (void*)&nspans, (void*)&err};
-  cudaLaunchKernel(warp_variant(thermo, mode), dim3(grid), dim3(BLOCK), args, 0, s);
+  cudaLaunchKernel(warp_variant(thermo, force, mode), dim3(grid), dim3(BLOCK), args, 0, s);
 }
 
 }  // namespace mpcd
