@@ -6,22 +6,27 @@
 // Same modes, records and results as k_cells (one thread per cell), for boxes
 // without walls or solute.  A warp owns 32 consecutive cells.  Their row
 // members are numbered 0 .. N-1 in cell order (a warp prefix sum of the row
-// counts) and lane j takes members j, j + 32, ...: every lane is busy and a
-// warp reads neighbouring records together, whatever the occupancy spread.
-//   pass 1   each member's rne(v 2^32) = H 2^20 + L (two int32 parts from two
-//            magic-number roundings) is summed per cell with segmented warp
-//            reductions (redux.sync over the lanes of one cell); the sums are
-//            exact, so u is the one of the per-cell loop
+// counts); a byte map gives each member's cell.
+//   pass 1   the velocities of up to 256 members are read in member order
+//            (neighbouring lanes read neighbouring records) into shared
+//            memory; then lane j takes a consecutive share of them, so its
+//            members lie in one or two cells.  Each velocity component gives
+//            rne(v 2^32) = H 2^20 + L, two int32 parts from two magic-number
+//            roundings, summed in registers while the cell stays the same
+//            and added to the cell's shared sums by one atomic per part when
+//            it changes.  The sums are exact, so u is the one of any order.
 //   cell     lane c turns the sums of cell c into u, draws the axis (and with
-//            the thermostat, after a second segmented pass for the energy
-//            about u, the factor xi) and leaves them in shared memory
-//   pass 2   each member collides with its cell's parameters, streams, is
-//            binned under the next shift and appended to its new row
+//            the thermostat, after the same kind of pass for the energy about
+//            u, the factor xi) and leaves them in shared memory
+//   pass 2   members in order across the lanes, two records in flight per
+//            lane: collide with the cell's parameters, stream, bin under the
+//            next shift, append to the new row
 // The parameters a member needs (time step, box, rotation, the thresholds of
 // the next grid shift, row pointers) are staged once per span in shared
 // memory.  Members beyond the row capacity (overflow list) stay with the lane
-// of their cell, as in k_cells.  The int32 parts stay in range while K <= 448 and
-// |v| < 1024; larger velocities take an exact int64 path through shared memory.
+// of their cell, as in k_cells.  The int32 parts stay in range while K <= 448
+// and |v| < 1024; a warp that meets a larger velocity (or energy) sums its
+// cells again in int64, one lane per cell.
 #include "dev_collide.cuh"
 #include "dev_rows.cuh"
 #include "dev_stream.cuh"
@@ -35,15 +40,16 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int WARPS = BLOCK / 32;
 
-constexpr int MAP_MEMBERS = 1024;
+constexpr int MAP_MEMBERS = 1024;  // members per warp with a byte owner map
+constexpr int STAGE = 256;         // member velocities staged per block of pass 1
 
 struct WarpShared {
-  int h[3][32];          // sum over the cell of H (momentum); h[0] reused for the energy
-  int l[3][32];          // sum of L
-  long long x[4][32];    // exact int64 sums of out-of-range members (momentum, energy)
-  float4 prm[2][32];     // (u, xi), (axis, 0) per cell
-  unsigned char own[32]; // lane of the cell whose first member sits at each window slot
+  float4 prm[2][32];               // (u, xi), (axis, 0) per cell
+  int h[3][32];                    // sum over the cell of H (momentum); h[0]: energy
+  int l[3][32];                    // sum of L
+  int offs[33];                    // first member of each cell; offs[32] = members
   unsigned char map[MAP_MEMBERS];  // owner lane of each member
+  float sv[3][STAGE];              // staged velocities
 };
 
 // rne(Q) as a float for Q = sh 2^20 + sl + x: one rounding of an exact sum of
@@ -52,14 +58,6 @@ __device__ __forceinline__ float split_sum_to_float(int sh, int sl, long long x)
   if (x == 0 && sh > -16777216 && sh < 16777216 && sl > -16777216 && sl < 16777216)
     return __fadd_rn(__int2float_rn(sh) * 1048576.0f, __int2float_rn(sl));
   return i64_to_float((long long)sh * 1048576LL + (long long)sl + x);
-}
-
-__device__ __forceinline__ void add_split(float v, int& H, int& L, long long* slow) {
-  if (!split32(v, H, L)) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(slow), (unsigned long long)fix32_rne(v));
-    H = 0;
-    L = 0;
-  }
 }
 
 // Per-span parameters shared by the block.
@@ -164,41 +162,59 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
     }
     const int off = incl - nrow;
     const int N = __shfl_sync(FULL, incl, 31);
+    W.offs[lane + 1] = incl;
+    if (lane == 0) W.offs[0] = 0;
     R* rows = H.rows_cur + (size_t)c0 * K;
     const R* ovf = (const R*)B.ovf_rec[cur];
     const uint32_t* ovf_cell = B.ovf_cell[cur];
     const uint32_t novf =
         __any_sync(FULL, has_ovf) ? min(B.ovf_n[cur], (uint32_t)B.ovf_cap) : 0u;
-
-    // Owner lane of every member: a byte map for up to MAP_MEMBERS members,
-    // else found per window of 32 (own[] holds the lanes whose first member
-    // falls in the window).
+    // owner lane of member m: a byte map for up to MAP_MEMBERS members, else a
+    // binary search of the offsets (the last cell whose first member is <= m)
     const bool mapped = N <= MAP_MEMBERS;
     if (mapped)
       for (int j = 0; j < nrow; ++j) W.map[off + j] = (unsigned char)lane;
     __syncwarp();
-    int carry = 0;
-    auto owner = [&](int base) -> int {  // warp-collective
-      if (mapped) return W.map[min(base + lane, N - 1)];
-      const int rel = off - base;
-      const bool st = nrow > 0 && rel >= 0 && rel < 32;
-      if (st) W.own[rel] = (unsigned char)lane;
-      const unsigned sb = __reduce_or_sync(FULL, st ? (1u << rel) : 0u);
-      __syncwarp();
-      const unsigned le = sb & (FULL >> (31 - lane));
-      const int o = le ? (int)W.own[31 - __clz(le)] : carry;
-      carry = __shfl_sync(FULL, o, 31);
-      __syncwarp();
-      return o;
+    auto owner_of = [&](int m) -> int {
+      if (mapped) return W.map[m];
+      int lo = 0, hi = 32;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (W.offs[mid] <= m) lo = mid;
+        else hi = mid;
+      }
+      return lo;
     };
-    // lanes of the same cell as this one within a window: from the heads
-    auto segment = [&](bool head) -> unsigned {
-      const unsigned hm = __ballot_sync(FULL, head || lane == 0);
-      const unsigned upto = FULL >> (31 - lane);
-      const int lo = 31 - __clz(hm & upto);
-      const unsigned gt = hm & ~upto;
-      const int hi = gt ? __ffs(gt) - 2 : 31;
-      return ((2u << hi) - 1u) & ~((1u << lo) - 1u);
+    auto member = [&](int m, int o) -> R* { return rows + (size_t)o * K + (m - W.offs[o]); };
+    // Velocities of members [sbase, sbase + cnt) into shared memory, read in
+    // member order (neighbouring lanes, neighbouring records).
+    auto stage = [&](int sbase, int cnt) {
+      for (int j = lane; j < cnt; j += 32) {
+        const float* p = reinterpret_cast<const float*>(member(sbase + j, owner_of(sbase + j)));
+        const float2 v12 = *reinterpret_cast<const float2*>(p + 4);
+        W.sv[0][j] = p[3];
+        W.sv[1][j] = v12.x;
+        W.sv[2][j] = v12.y;
+      }
+      __syncwarp();
+    };
+    // This lane's consecutive share of a staged block: f(o, j, last) with the
+    // owner lane o, the index j in the block and whether j is the last of the
+    // share in cell o.
+    auto share = [&](int sbase, int cnt, auto&& f) {
+      const int cs = (lane * cnt) >> 5, ce = ((lane + 1) * cnt) >> 5;
+      if (cs >= ce) return;
+      int o = owner_of(sbase + cs);
+      int cend = W.offs[o + 1] - sbase;
+      for (int j = cs; j < ce; ++j) {
+        if (j == cend) {
+          do {
+            ++o;
+            cend = W.offs[o + 1] - sbase;
+          } while (cend == j);
+        }
+        f(o, j, j + 1 == cend || j + 1 == ce);
+      }
     };
 
     if (MODE != MODE_P) {
@@ -207,53 +223,63 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
       for (int q = 0; q < 3; ++q) {
         W.h[q][lane] = 0;
         W.l[q][lane] = 0;
-        W.x[q][lane] = 0;
       }
-      W.x[3][lane] = 0;
       __syncwarp();
-      for (int base = 0; base < N; base += 32) {
-        const int o = owner(base);
-        const int k = base + lane - __shfl_sync(FULL, off, o);
-        const bool act = base + lane < N;
+      bool slow = false;
+      for (int sbase = 0; sbase < N; sbase += STAGE) {
+        const int cnt = min(STAGE, N - sbase);
+        stage(sbase, cnt);
         int Hs[3] = {0, 0, 0}, Ls[3] = {0, 0, 0};
-        if (act) {
-          const float* p = reinterpret_cast<const float*>(rows + (size_t)o * K + k);
-          const float v0 = p[3];
-          const float2 v12 = *reinterpret_cast<const float2*>(p + 4);
-          add_split(v0, Hs[0], Ls[0], &W.x[0][o]);
-          add_split(v12.x, Hs[1], Ls[1], &W.x[1][o]);
-          add_split(v12.y, Hs[2], Ls[2], &W.x[2][o]);
-        }
-        const bool head = act && k == 0;
-        const unsigned seg = segment(head);
+        share(sbase, cnt, [&](int o, int j, bool last) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const int sh = __reduce_add_sync(seg, Hs[q]);
-          const int sl = __reduce_add_sync(seg, Ls[q]);
-          if (head || lane == 0) {
-            W.h[q][o] += sh;
-            W.l[q][o] += sl;
+          for (int q = 0; q < 3; ++q) {
+            int h, l;
+            if (!split32(W.sv[q][j], h, l)) {
+              slow = true;
+              h = 0;
+              l = 0;
+            }
+            Hs[q] += h;
+            Ls[q] += l;
           }
-        }
+          if (last) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              atomicAdd(&W.h[q][o], Hs[q]);
+              atomicAdd(&W.l[q][o], Ls[q]);
+              Hs[q] = 0;
+              Ls[q] = 0;
+            }
+          }
+        });
         __syncwarp();
       }
+      const bool exact64 = __any_sync(FULL, slow);  // a velocity of 1024 or more
 
       // ---- per cell: u (Sec. 3.5), then the energy about u, axis and xi ----
       float u[3] = {0.0f, 0.0f, 0.0f};
-      long long ovq[3] = {0, 0, 0};
-      if (has_ovf)
-        for (uint32_t j = 0; j < novf; ++j)
-          if (ovf_cell[j] == (uint32_t)cell) {
-            float w[3];
-            load_v(ovf + j, w);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) ovq[q] += fix32_rne(w[q]);
-          }
       if (n > 0) {
+        long long Q[3] = {0, 0, 0};
+        if (exact64)
+          for (int k = 0; k < nrow; ++k) {
+            float w[3];
+            load_v(rows + (size_t)lane * K + k, w);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Q[q] += fix32_rne(w[q]);
+          }
+        if (has_ovf)
+          for (uint32_t j = 0; j < novf; ++j)
+            if (ovf_cell[j] == (uint32_t)cell) {
+              float w[3];
+              load_v(ovf + j, w);
+#pragma unroll
+              for (int q = 0; q < 3; ++q) Q[q] += fix32_rne(w[q]);
+            }
         const float M = H.m * small_to_float((int)n);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          const float P = H.m * split_sum_to_float(W.h[q][lane], W.l[q][lane], W.x[q][lane] + ovq[q]);
+          const float P = H.m * (exact64 ? i64_to_float(Q[q])
+                                         : split_sum_to_float(W.h[q][lane], W.l[q][lane], Q[q]));
           u[q] = (P * 0x1p-32f) / M;
         }
         W.prm[0][lane] = make_float4(u[0], u[1], u[2], 1.0f);
@@ -263,42 +289,49 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         W.h[0][lane] = 0;
         W.l[0][lane] = 0;
         __syncwarp();
-        for (int base = 0; base < N; base += 32) {
-          const int o = owner(base);
-          const int k = base + lane - __shfl_sync(FULL, off, o);
-          const bool act = base + lane < N;
+        bool slow_e = false;
+        for (int sbase = 0; sbase < N; sbase += STAGE) {
+          const int cnt = min(STAGE, N - sbase);
+          if (N > STAGE) stage(sbase, cnt);  // else still staged from pass 1
           int He = 0, Le = 0;
-          if (act) {
-            const float* p = reinterpret_cast<const float*>(rows + (size_t)o * K + k);
-            const float v0 = p[3];
-            const float2 v12 = *reinterpret_cast<const float2*>(p + 4);
+          share(sbase, cnt, [&](int o, int j, bool last) {
             const float4 uo = W.prm[0][o];
-            const float d0 = v0 - uo.x, d1 = v12.x - uo.y, d2 = v12.y - uo.z;
-            const float e = d0 * d0 + d1 * d1 + d2 * d2;
-            add_split(e, He, Le, &W.x[3][o]);
-          }
-          const bool head = act && k == 0;
-          const unsigned seg = segment(head);
-          const int sh = __reduce_add_sync(seg, He);
-          const int sl = __reduce_add_sync(seg, Le);
-          if (head || lane == 0) {
-            W.h[0][o] += sh;
-            W.l[0][o] += sl;
-          }
+            const float d0 = W.sv[0][j] - uo.x, d1 = W.sv[1][j] - uo.y, d2 = W.sv[2][j] - uo.z;
+            const float en = d0 * d0 + d1 * d1 + d2 * d2;
+            int h, l;
+            if (!split32(en, h, l)) {
+              slow_e = true;
+              h = 0;
+              l = 0;
+            }
+            He += h;
+            Le += l;
+            if (last) {
+              atomicAdd(&W.h[0][o], He);
+              atomicAdd(&W.l[0][o], Le);
+              He = 0;
+              Le = 0;
+            }
+          });
           __syncwarp();
         }
+        const bool exact64_e = __any_sync(FULL, slow_e);
         if (n > 0) {
-          long long ove = 0;
+          long long Es = 0;
+          auto add_energy = [&](const R* p) {
+            float w[3];
+            load_v(p, w);
+            const float d0 = w[0] - u[0], d1 = w[1] - u[1], d2 = w[2] - u[2];
+            Es += fix32_rne(d0 * d0 + d1 * d1 + d2 * d2);
+          };
+          if (exact64_e)
+            for (int k = 0; k < nrow; ++k) add_energy(rows + (size_t)lane * K + k);
           if (has_ovf)
             for (uint32_t j = 0; j < novf; ++j)
-              if (ovf_cell[j] == (uint32_t)cell) {
-                float w[3];
-                load_v(ovf + j, w);
-                const float d0 = w[0] - u[0], d1 = w[1] - u[1], d2 = w[2] - u[2];
-                ove += fix32_rne(d0 * d0 + d1 * d1 + d2 * d2);
-              }
+              if (ovf_cell[j] == (uint32_t)cell) add_energy(ovf + j);
           // Eq. thermo: E_k about u, E^ ~ Gamma(3(n-1)/2, kT), xi = sqrt(E^/E_k)
-          const float E = H.m * split_sum_to_float(W.h[0][lane], W.l[0][lane], W.x[3][lane] + ove);
+          const float E = H.m * (exact64_e ? i64_to_float(Es)
+                                           : split_sum_to_float(W.h[0][lane], W.l[0][lane], Es));
           const float Ek = (0.5f * E) * 0x1p-32f;
           if (n >= 2 && Ek > 0.0f) {
             float ehat;
@@ -373,19 +406,26 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         }
       }
     };
-    // two windows per iteration: both records are in flight together
+    // members in order across the lanes, two windows of 32 per iteration so
+    // that both records are in flight together
     for (int base = 0; base < N; base += 64) {
-      const int oa = owner(base);
-      const int ob = base + 32 < N ? owner(base + 32) : 0;
-      const int ka = base + lane - __shfl_sync(FULL, off, oa);
-      const int kb = base + 32 + lane - __shfl_sync(FULL, off, ob);
-      const bool acta = base + lane < N, actb = base + 32 + lane < N;
+      const int ma = base + lane, mb = base + 32 + lane;
+      const bool acta = ma < N, actb = mb < N;
       float ra[3], wa[3], rb[3], wb[3];
       uint32_t taga = 0u, tagb = 0u;
-      R* pa = rows + (size_t)oa * K + ka;
-      R* pb = rows + (size_t)ob * K + kb;
-      if (acta) load_rec(pa, ra, wa, taga);
-      if (actb) load_rec(pb, rb, wb, tagb);
+      int oa = 0, ob = 0;
+      R* pa = rows;
+      R* pb = rows;
+      if (acta) {
+        oa = owner_of(ma);
+        pa = member(ma, oa);
+        load_rec(pa, ra, wa, taga);
+      }
+      if (actb) {
+        ob = owner_of(mb);
+        pb = member(mb, ob);
+        load_rec(pb, rb, wb, tagb);
+      }
       if (acta) finish(pa, ra, wa, taga, oa);
       if (actb) finish(pb, rb, wb, tagb, ob);
     }
