@@ -298,8 +298,10 @@ def main():
     dom = "fused_step"
     dom_ms = phases[dom]
     achieved = step_bytes * s.pos.shape[0] / (dom_ms * 1e-3) / 1e9
-    traffic = kernel_traffic("k_cells", args.workload)
-    roofline = {"bound": "hbm", "kernel": "k_cells (collide t + stream/bin t+1)",
+    # the warp-spread kernel runs mixed-model boxes without walls or solute
+    kname = "k_cells_warp" if cfg["precision"] == "mixed" and not cfg.get("n_chains") else "k_cells"
+    traffic = kernel_traffic(kname, args.workload)
+    roofline = {"bound": "hbm", "kernel": f"{kname} (collide t + stream/bin t+1)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
                 "alg_bytes_per_particle": step_bytes}

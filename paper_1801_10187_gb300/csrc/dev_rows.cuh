@@ -10,16 +10,23 @@ namespace mpcd {
 template <bool MIXED>
 using rec_t = typename std::conditional<MIXED, RecF, RecD>::type;
 
+// A mixed-model record is one 32-byte sector, moved by one 256-bit access
+// (records are 32-byte aligned: row bases are allocation-aligned and every
+// row and slot is a multiple of 32 bytes).
 __device__ __forceinline__ void load_rec(const RecF* p, float r[3], float v[3], uint32_t& tag) {
-  const float4 a = reinterpret_cast<const float4*>(p)[0];
-  const float4 b = reinterpret_cast<const float4*>(p)[1];
-  r[0] = a.x; r[1] = a.y; r[2] = a.z;
-  v[0] = a.w; v[1] = b.x; v[2] = b.y;
-  tag = __float_as_uint(b.z);
+  float t;
+  [[maybe_unused]] float pad;
+  asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(v[0]), "=f"(v[1]), "=f"(v[2]),
+                 "=f"(t), "=f"(pad)
+               : "l"(p));
+  tag = __float_as_uint(t);
 }
 __device__ __forceinline__ void store_rec(RecF* p, const float r[3], const float v[3], uint32_t tag) {
-  reinterpret_cast<float4*>(p)[0] = make_float4(r[0], r[1], r[2], v[0]);
-  reinterpret_cast<float4*>(p)[1] = make_float4(v[1], v[2], __uint_as_float(tag), 0.0f);
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(r[0]),
+               "f"(r[1]), "f"(r[2]), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(__uint_as_float(tag)),
+               "f"(0.0f)
+               : "memory");
 }
 __device__ __forceinline__ void load_rec(const RecD* p, double r[3], double v[3], uint32_t& tag) {
   const double2 a = reinterpret_cast<const double2*>(p)[0];

@@ -20,10 +20,12 @@
 //            u, the factor xi) and leaves them in shared memory
 //   pass 2   members in order across the lanes, two records in flight per
 //            lane: collide with the cell's parameters, stream, bin under the
-//            next shift, append to the new row
+//            next shift, take a slot in the new row and write the record
+//            there; lanes bound for the same cell share one atomic on its
+//            count (match.any), which cuts the slot requests about threefold
 // The parameters a member needs (time step, box, rotation, the thresholds of
-// the next grid shift, row pointers) are staged once per span in shared
-// memory.  Members beyond the row capacity (overflow list) stay with the lane
+// the next grid shift, row pointers) are staged in shared memory when a block
+// meets a new box.  Members beyond the row capacity (overflow list) stay with the lane
 // of their cell, as in k_cells.  The int32 parts stay in range while K <= 448
 // and |v| < 1024; a warp that meets a larger velocity (or energy) sums its
 // cells again in int64, one lane per cell.
@@ -40,17 +42,24 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int WARPS = BLOCK / 32;
 
-constexpr int MAP_MEMBERS = 1024;  // members per warp with a byte owner map
-constexpr int STAGE = 256;         // member velocities staged per block of pass 1
+constexpr int MAP_MEMBERS = 640;  // members per warp with a byte owner map
+constexpr int STAGE = 256;        // member velocities staged per block of pass 1
+constexpr int STAGE_PAD = STAGE + STAGE / 32;
 
 struct WarpShared {
   float4 prm[2][32];               // (u, xi), (axis, 0) per cell
   int h[3][32];                    // sum over the cell of H (momentum); h[0]: energy
   int l[3][32];                    // sum of L
   int offs[33];                    // first member of each cell; offs[32] = members
+  int pad_[3];
   unsigned char map[MAP_MEMBERS];  // owner lane of each member
-  float sv[3][STAGE];              // staged velocities
+  float sv[3][STAGE_PAD];          // staged velocities (index j + j / 32)
 };
+
+// Shared memory of one block: the span parameters, then one area per warp;
+// kept under 48 KB so that four blocks (the register limit) fit on an SM with
+// room left for L1.
+constexpr size_t WARP_SMEM = sizeof(WarpShared);
 
 // rne(Q) as a float for Q = sh 2^20 + sl + x: one rounding of an exact sum of
 // two exact floats when the parts are small (always, for real velocities).
@@ -74,6 +83,8 @@ struct SpanParams {
   uint32_t* ovf_n_out;
   int ovf_cap, pad;
 };
+constexpr size_t SPAN_SMEM = (sizeof(SpanParams) + 15) & ~(size_t)15;
+constexpr size_t BLOCK_SMEM = SPAN_SMEM + WARPS * WARP_SMEM;
 
 // floor(x - s) for 0 <= x < 2^22 and s = S 2^-32 in [-1/2, 1/2), exactly:
 // x = i0 + f with i0 = floor(x) (round-down add of 2^23) and f exact; then
@@ -112,38 +123,43 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
                                                          const int2* __restrict__ spans,
                                                          int nspans, int* err) {
   using R = RecF;
-  __shared__ WarpShared shw[WARPS];
-  __shared__ SpanParams sp_;
+  extern __shared__ __align__(16) unsigned char smem_[];
+  SpanParams& sp_ = *reinterpret_cast<SpanParams*>(smem_);
   const int lane = threadIdx.x & 31;
-  WarpShared& W = shw[threadIdx.x >> 5];
+  WarpShared& W =
+      reinterpret_cast<WarpShared*>(smem_ + SPAN_SMEM)[threadIdx.x >> 5];
   const SpanParams& H = sp_;
+  int box_of_params = -1;  // the span parameters depend on the box only
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
     const int2 tt = spans[sp];
     const BoxDev& B = boxes[tt.x];
     const unsigned long long t = B.step;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      SpanParams& P = sp_;
-      P.dt = B.dt_f; P.ca = B.ca_f; P.sa = B.sa_f; P.omc = B.omc_f; P.m = B.m_f;
-      for (int q = 0; q < 3; ++q) {
-        P.L[q] = B.L_f[q]; P.hg[q] = B.hg_f[q]; P.gdt[q] = B.gdt_f[q]; P.n[q] = B.n[q];
+    if (tt.x != box_of_params) {  // block-uniform
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        SpanParams& P = sp_;
+        P.dt = B.dt_f; P.ca = B.ca_f; P.sa = B.sa_f; P.omc = B.omc_f; P.m = B.m_f;
+        for (int q = 0; q < 3; ++q) {
+          P.L[q] = B.L_f[q]; P.hg[q] = B.hg_f[q]; P.gdt[q] = B.gdt_f[q]; P.n[q] = B.n[q];
+        }
+        P.K = B.K;
+        const int out = B.cur ^ 1;
+        P.rows_cur = (RecF*)B.rows[B.cur];
+        P.rows_out = (RecF*)B.rows[out];
+        P.cnt_out = B.cnt[out];
+        P.ovf_out = (RecF*)B.ovf_rec[out];
+        P.ovf_cell_out = B.ovf_cell[out];
+        P.ovf_n_out = &B.ovf_n[out];
+        P.ovf_cap = B.ovf_cap;
+        if (MODE != MODE_C) {
+          long long S[3];
+          shift_units(B, MODE == MODE_P ? t : t + 1ull, S);
+          for (int q = 0; q < 3; ++q) bin_thresholds(S[q], P.lo[q], P.hi[q]);
+        }
       }
-      P.K = B.K;
-      const int out = B.cur ^ 1;
-      P.rows_cur = (RecF*)B.rows[B.cur];
-      P.rows_out = (RecF*)B.rows[out];
-      P.cnt_out = B.cnt[out];
-      P.ovf_out = (RecF*)B.ovf_rec[out];
-      P.ovf_cell_out = B.ovf_cell[out];
-      P.ovf_n_out = &B.ovf_n[out];
-      P.ovf_cap = B.ovf_cap;
-      if (MODE != MODE_C) {
-        long long S[3];
-        shift_units(B, MODE == MODE_P ? t : t + 1ull, S);
-        for (int q = 0; q < 3; ++q) bin_thresholds(S[q], P.lo[q], P.hi[q]);
-      }
+      __syncthreads();
+      box_of_params = tt.x;
     }
-    __syncthreads();
     const int c0 = tt.y + (int)(threadIdx.x & ~31u);
     if (c0 >= B.ncells) continue;  // warp-uniform
     const int cell = c0 + lane;
@@ -162,6 +178,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
     }
     const int off = incl - nrow;
     const int N = __shfl_sync(FULL, incl, 31);
+    __syncwarp();  // the previous span of this warp is done with W
     W.offs[lane + 1] = incl;
     if (lane == 0) W.offs[0] = 0;
     R* rows = H.rows_cur + (size_t)c0 * K;
@@ -192,15 +209,16 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
       for (int j = lane; j < cnt; j += 32) {
         const float* p = reinterpret_cast<const float*>(member(sbase + j, owner_of(sbase + j)));
         const float2 v12 = *reinterpret_cast<const float2*>(p + 4);
-        W.sv[0][j] = p[3];
-        W.sv[1][j] = v12.x;
-        W.sv[2][j] = v12.y;
+        const int js = j + (j >> 5);
+        W.sv[0][js] = p[3];
+        W.sv[1][js] = v12.x;
+        W.sv[2][js] = v12.y;
       }
       __syncwarp();
     };
-    // This lane's consecutive share of a staged block: f(o, j, last) with the
-    // owner lane o, the index j in the block and whether j is the last of the
-    // share in cell o.
+    // This lane's consecutive share of a staged block: f(o, js, last) with the
+    // owner lane o, the (padded) index js in the block and whether it is the
+    // last of the share in cell o.
     auto share = [&](int sbase, int cnt, auto&& f) {
       const int cs = (lane * cnt) >> 5, ce = ((lane + 1) * cnt) >> 5;
       if (cs >= ce) return;
@@ -213,7 +231,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
             cend = W.offs[o + 1] - sbase;
           } while (cend == j);
         }
-        f(o, j, j + 1 == cend || j + 1 == ce);
+        f(o, j + (j >> 5), j + 1 == cend || j + 1 == ce);
       }
     };
 
@@ -230,11 +248,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         const int cnt = min(STAGE, N - sbase);
         stage(sbase, cnt);
         int Hs[3] = {0, 0, 0}, Ls[3] = {0, 0, 0};
-        share(sbase, cnt, [&](int o, int j, bool last) {
+        share(sbase, cnt, [&](int o, int js, bool last) {
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             int h, l;
-            if (!split32(W.sv[q][j], h, l)) {
+            if (!split32(W.sv[q][js], h, l)) {
               slow = true;
               h = 0;
               l = 0;
@@ -294,9 +312,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
           const int cnt = min(STAGE, N - sbase);
           if (N > STAGE) stage(sbase, cnt);  // else still staged from pass 1
           int He = 0, Le = 0;
-          share(sbase, cnt, [&](int o, int j, bool last) {
+          share(sbase, cnt, [&](int o, int js, bool last) {
             const float4 uo = W.prm[0][o];
-            const float d0 = W.sv[0][j] - uo.x, d1 = W.sv[1][j] - uo.y, d2 = W.sv[2][j] - uo.z;
+            const float d0 = W.sv[0][js] - uo.x, d1 = W.sv[1][js] - uo.y, d2 = W.sv[2][js] - uo.z;
             const float en = d0 * d0 + d1 * d1 + d2 * d2;
             int h, l;
             if (!split32(en, h, l)) {
@@ -350,7 +368,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
     }
 
     // ---- pass 2: collide (Eq. srd), stream (Eq. stream), bin (Sec. 3.4) ----
-    auto finish = [&](R* p, float r[3], float w[3], uint32_t tag, int o) {
+    // new state of a member and its cell for the next step
+    auto advance = [&](float r[3], float w[3], int o) -> uint32_t {
       if (MODE != MODE_P) {
         const float4 pa = W.prm[0][o], pb = W.prm[1][o];
         const float nn[3] = {pb.x, pb.y, pb.z};
@@ -362,10 +381,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
 #pragma unroll
         for (int q = 0; q < 3; ++q) w[q] = uu[q] + (THERMO ? pa.w * rr[q] : rr[q]);
       }
-      if (MODE == MODE_C) {
-        store_rec(p, r, w, tag);
-        return;
-      }
+      if (MODE == MODE_C) return 0u;
       // periodic box; the additions of zero keep the operation sequence of
       // the general form (they turn -0 into +0)
       bool bad = false;
@@ -392,8 +408,11 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
       const int cx = bin_axis(r[0], H.lo[0], H.hi[0], H.n[0]);
       const int cy = bin_axis(r[1], H.lo[1], H.hi[1], H.n[1]);
       const int cz = bin_axis(r[2], H.lo[2], H.hi[2], H.n[2]);
-      const uint32_t c2 = (uint32_t)(cx + H.n[0] * (cy + H.n[1] * cz));
-      const uint32_t slot = atomicAdd(&H.cnt_out[c2], 1u);
+      return (uint32_t)(cx + H.n[0] * (cy + H.n[1] * cz));
+    };
+    // append a record to the row of cell c2 at the slot taken for it (or to
+    // the overflow list beyond the row capacity)
+    auto emit = [&](const float r[3], const float w[3], uint32_t tag, uint32_t c2, uint32_t slot) {
       if (slot < (uint32_t)H.K) {
         store_rec(H.rows_out + (size_t)c2 * H.K + slot, r, w, tag);
       } else {
@@ -406,28 +425,67 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         }
       }
     };
-    // members in order across the lanes, two windows of 32 per iteration so
-    // that both records are in flight together
-    for (int base = 0; base < N; base += 64) {
-      const int ma = base + lane, mb = base + 32 + lane;
-      const bool acta = ma < N, actb = mb < N;
-      float ra[3], wa[3], rb[3], wb[3];
-      uint32_t taga = 0u, tagb = 0u;
-      int oa = 0, ob = 0;
-      R* pa = rows;
-      R* pb = rows;
-      if (acta) {
-        oa = owner_of(ma);
-        pa = member(ma, oa);
-        load_rec(pa, ra, wa, taga);
+    if (MODE == MODE_C) {
+      // collide in place, two records in flight per lane
+      for (int base = 0; base < N; base += 64) {
+        const int ma = base + lane, mb = base + 32 + lane;
+        float ra[3], wa[3], rb[3], wb[3];
+        uint32_t ta = 0u, tb = 0u;
+        int oa = 0, ob = 0;
+        R* pa = rows;
+        R* pb = rows;
+        if (ma < N) {
+          oa = owner_of(ma);
+          pa = member(ma, oa);
+          load_rec(pa, ra, wa, ta);
+        }
+        if (mb < N) {
+          ob = owner_of(mb);
+          pb = member(mb, ob);
+          load_rec(pb, rb, wb, tb);
+        }
+        if (ma < N) {
+          advance(ra, wa, oa);
+          store_rec(pa, ra, wa, ta);
+        }
+        if (mb < N) {
+          advance(rb, wb, ob);
+          store_rec(pb, rb, wb, tb);
+        }
       }
-      if (actb) {
-        ob = owner_of(mb);
-        pb = member(mb, ob);
-        load_rec(pb, rb, wb, tagb);
+    } else {
+      // Slots in the new rows: the lanes of a window that go to the same cell
+      // take consecutive slots with one atomic, made by the first of them.
+      auto take_slot = [&](bool act, uint32_t c2) -> uint32_t {
+        const unsigned peers = __match_any_sync(FULL, act ? c2 : 0xFFFFFFFFu);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0u;
+        if (act && lane == leader) base = atomicAdd(&H.cnt_out[c2], (uint32_t)__popc(peers));
+        base = __shfl_sync(FULL, base, leader);
+        return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+      };
+      // two records in flight per lane
+      for (int base = 0; base < N; base += 64) {
+        const int ma = base + lane, mb = base + 32 + lane;
+        const bool acta = ma < N, actb = mb < N;
+        float ra[3], wa[3], rb[3], wb[3];
+        uint32_t ta = 0u, tb = 0u, ca = 0u, cb = 0u;
+        int oa = 0, ob = 0;
+        if (acta) {
+          oa = owner_of(ma);
+          load_rec(member(ma, oa), ra, wa, ta);
+        }
+        if (actb) {
+          ob = owner_of(mb);
+          load_rec(member(mb, ob), rb, wb, tb);
+        }
+        if (acta) ca = advance(ra, wa, oa);
+        if (actb) cb = advance(rb, wb, ob);
+        const uint32_t sa = take_slot(acta, ca);
+        const uint32_t sb = take_slot(actb, cb);
+        if (acta) emit(ra, wa, ta, ca, sa);
+        if (actb) emit(rb, wb, tb, cb, sb);
       }
-      if (acta) finish(pa, ra, wa, taga, oa);
-      if (actb) finish(pb, rb, wb, tagb, ob);
     }
     if (has_ovf) {
       for (uint32_t j = 0; j < novf; ++j)
@@ -436,7 +494,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
           float r[3], w[3];
           uint32_t tag;
           load_rec(p, r, w, tag);
-          finish(p, r, w, tag, lane);
+          const uint32_t c2 = advance(r, w, lane);
+          if (MODE == MODE_C) store_rec(p, r, w, tag);
+          else emit(r, w, tag, c2, atomicAdd(&H.cnt_out[c2], 1u));
         }
     }
   }
@@ -460,8 +520,10 @@ static void* warp_variant(bool thermo, bool force, int mode) {
 }
 
 int cells_warp_blocks_per_sm(bool thermo, bool force, int mode) {
+  const void* fn = warp_variant(thermo, force, mode);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BLOCK_SMEM);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, warp_variant(thermo, force, mode), BLOCK, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, BLOCK_SMEM);
   return nb;
 }
 
@@ -469,7 +531,7 @@ void launch_cells_warp(bool thermo, bool force, int mode, const BoxDev* boxes, c
                        int nspans, int grid, int* err, cudaStream_t s) {
   if (nspans <= 0) return;
   void* args[] = {(void*)&boxes, (void*)&spans, (void*)&nspans, (void*)&err};
-  cudaLaunchKernel(warp_variant(thermo, force, mode), dim3(grid), dim3(BLOCK), args, 0, s);
+  cudaLaunchKernel(warp_variant(thermo, force, mode), dim3(grid), dim3(BLOCK), args, BLOCK_SMEM, s);
 }
 
 }  // namespace mpcd
