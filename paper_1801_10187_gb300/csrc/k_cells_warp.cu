@@ -206,13 +206,28 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
     // Velocities of members [sbase, sbase + cnt) into shared memory, read in
     // member order (neighbouring lanes, neighbouring records).
     auto stage = [&](int sbase, int cnt) {
-      for (int j = lane; j < cnt; j += 32) {
-        const float* p = reinterpret_cast<const float*>(member(sbase + j, owner_of(sbase + j)));
-        const float2 v12 = *reinterpret_cast<const float2*>(p + 4);
-        const int js = j + (j >> 5);
-        W.sv[0][js] = p[3];
-        W.sv[1][js] = v12.x;
-        W.sv[2][js] = v12.y;
+      for (int j0 = 0; j0 < cnt; j0 += 128) {  // four windows of loads in flight
+        float a[4];
+        float2 b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + (u << 5) + lane;
+          if (j < cnt) {
+            const float* p = reinterpret_cast<const float*>(member(sbase + j, owner_of(sbase + j)));
+            a[u] = p[3];
+            b[u] = *reinterpret_cast<const float2*>(p + 4);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + (u << 5) + lane;
+          if (j < cnt) {
+            const int js = j + (j >> 5);
+            W.sv[0][js] = a[u];
+            W.sv[1][js] = b[u].x;
+            W.sv[2][js] = b[u].y;
+          }
+        }
       }
       __syncwarp();
     };
