@@ -210,10 +210,15 @@ def main():
     ap.add_argument("--workload", default="srd-100c-rho10-mixed")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--jobs", type=int, default=None, help="served workload: number of jobs")
+    ap.add_argument("--no-sweep", action="store_true", help="served workload: skip the rate sweep")
     args = ap.parse_args()
     cfg = workload_cfg(args.workload)
-    K = args.steps if args.steps is not None else cfg["steps"]
+    kind = cfg.get("kind", "box")
+    K = args.steps if args.steps is not None else cfg.get("steps", 0)
     W = max(3, args.warmup)
+    if kind != "box":
+        return run_fleet(args, cfg, kind, K, W)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -356,6 +361,189 @@ def main():
     box.close()
     if dist:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ batched / served
+def _fleet_reference(args, cfg, kind, K, W):
+    """Oracle timing for the batch and served workloads: one of their boxes
+    (a 16^3-cell box at density 5, the smallest ensemble member) as the
+    bounded sample."""
+    sub = dict(n=(16, 16, 16), density=5, dt=cfg["dt"] if "dt" in cfg else 0.1, kT=1.0,
+               alpha_deg=130.0, seed=1000, thermostat=False, precision=cfg["precision"])
+    rate, sample, dt, nsteps = oracle_rate(sub, 150.0, steps=max(1, min(K or 5, 20)), warmup=0)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / nsteps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+i64", "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_fleet(args, cfg, kind, K, W):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            _fleet_reference(args, cfg, kind, K, W)
+        return
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    import paper_1801_10187_gb300 as pkg
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sampler = ClockSampler(local_rank)
+    if kind == "batch":
+        line = _run_batch(pkg, torch, stream, sampler, args, cfg, K, W, rank, world, dist)
+    else:
+        line = _run_serve(pkg, torch, stream, sampler, args, cfg, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def _run_batch(pkg, torch, stream, sampler, args, cfg, K, W, rank, world, dist):
+    """All boxes of the ensemble in one batch (one fused launch per step for
+    every box), against the same boxes stepped one after another as plain
+    single-box contexts.  Thermal initial states are drawn on the device."""
+    specs = inputs.ensemble(cfg["n_boxes"], seed=cfg["ensemble_seed"])
+    common = dict(dt=cfg["dt"], kT=cfg["kT"], thermostat=cfg["thermostat"],
+                  precision=cfg["precision"])
+    counts = [int(round(s["density"] * np.prod(s["n"]))) for s in specs]
+    N = sum(counts)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # ---- batched ----
+    batch = pkg.Batch(cfg["precision"], stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    for s, n in zip(specs, counts):
+        batch.add_thermal(n, init_seed=s["seed"] + rank * 100000, n=s["n"],
+                          alpha_deg=s["alpha_deg"], seed=s["seed"] + rank * 100000, **common)
+    batch.step(W)
+    batch.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    batch.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    obs = [batch.observables(i) for i in range(len(specs))]
+    wall = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([ms, wall], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, wall = float(t[0].item()), float(t[1].item())
+    batched = N * K * world / (ms * 1e-3)
+    assert all(o["step"] == W + K for o in obs)
+    batch.close()
+
+    # ---- per-box plain launches, one box after another ----
+    per_ms = 0.0
+    for s, n in zip(specs, counts):
+        box = pkg.Box(stream=stream.cuda_stream, n=s["n"], alpha_deg=s["alpha_deg"],
+                      seed=s["seed"] + rank * 100000, **common)
+        box.set_state_thermal(n, init_seed=s["seed"] + rank * 100000)
+        box.step(W)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        box.step(K)
+        b.record(stream)
+        torch.cuda.synchronize()
+        per_ms += a.elapsed_time(b)
+        box.close()
+    if dist:
+        t = torch.tensor([per_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        per_ms = float(t.item())
+    per_box = N * K * world / (per_ms * 1e-3)
+    es = 4 if cfg["precision"] == "mixed" else 8
+    step_bytes = 2 * 3 * es + 3 * 3 * es
+    peak, src = load_peaks()
+    gbs = step_bytes * N * K / (ms * 1e-3) / 1e9
+    return {"metric": METRIC, "value": batched, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+i64" if cfg["precision"] == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "boxes": len(specs), "particles": N,
+                       "recipe": "inputs.ensemble(64, seed=4): L in U{16..96}, density 5|10, "
+                                 "angle 90|120|130 deg, seeds 1000+i, thermal states on device",
+                       "l2": f"state {N * 6 * es / 1e9:.1f} GB > 129 MB L2 (no flush)"},
+            "clocks": clocks,
+            "per_box_plain_launches": {"value": per_box, "unit": UNIT, "ms_total": per_ms,
+                                       "ratio_batched_over_per_box": batched / per_box},
+            "e2e": {"value": N * K * world / wall, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": len(specs) * 96 / K,
+                    "note": "add_thermal (states drawn on device) + warm-up + K steps + "
+                            "observables of every box, wall clock"},
+            "gpu_launches": 2 * K,
+            "roofline": {"bound": "hbm", "kernel": "k_cells_warp (all boxes in one launch)",
+                         "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "traffic": None, "peak_source": src,
+                         "alg_bytes_per_particle": step_bytes},
+            "cpu_baseline": None}
+
+
+def _run_serve(pkg, torch, stream, sampler, args, cfg, rank, world, dist):
+    """The served workload: Poisson job arrivals, admission by device-memory
+    footprint, every resident job advanced in one batch; p50/p99 latency and
+    aggregate throughput, then a sweep of arrival rates below saturation."""
+    from paper_1801_10187_gb300 import serve
+    n_jobs = args.jobs if args.jobs is not None else cfg["n_jobs"]
+    free, _total = torch.cuda.mem_get_info()
+    budget = int(free * 0.8)
+
+    def one(rate, nj, seed):
+        jobs = serve.poisson_jobs(nj, rate, seed=seed, l_min=cfg["l_min"], l_max=cfg["l_max"],
+                                  density=cfg["density"], steps_min=cfg["steps_min"],
+                                  steps_max=cfg["steps_max"], alpha_deg=cfg["alpha_deg"])
+        srv = serve.Server(precision=cfg["precision"], max_bytes=budget,
+                           stream=stream.cuda_stream)
+        st = srv.run(jobs, realtime=True)
+        srv.close()
+        d = st.as_dict()
+        d["rate_jobs_per_s"] = rate
+        return d
+
+    if dist:
+        dist.barrier()
+    sampler.start()
+    main_run = one(cfg["rate"], n_jobs, cfg["jobs_seed"] + rank)
+    clocks = sampler.stop()
+    sweep = []
+    if not args.no_sweep:
+        for r in cfg["sweep_rates"]:
+            sweep.append(one(r, cfg["sweep_jobs"], cfg["jobs_seed"] + 100 + rank))
+    value = main_run["particle_steps_per_s"]
+    if dist:
+        t = torch.tensor([main_run["makespan_s"]], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        value = main_run["particle_steps"] * world / float(t.item())
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": None, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
+            "config": {"workload": args.workload, "jobs": n_jobs, "rate_jobs_per_s": cfg["rate"],
+                       "recipe": "serve.poisson_jobs: L log-uniform [10,160], density 5, steps "
+                                 "U[100,5000], 130 deg, thermostat on every other job",
+                       "admission_bytes": budget},
+            "clocks": clocks, "served": main_run, "sweep": sweep,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0,
+                    "note": "wall clock of the whole served run through the public API"},
+            "gpu_launches": None, "roofline": None, "cpu_baseline": None}
 
 
 if __name__ == "__main__":

@@ -80,6 +80,20 @@ def chains(n_cells, n_chains: int, chain_len: int, r0: float, kT: float = 1.0,
     return np.ascontiguousarray(pos), np.ascontiguousarray(vel)
 
 
+def ensemble(n_boxes: int = 64, seed: int = 4) -> list:
+    """Batched-ensemble recipe: independent periodic cubic boxes, edge L
+    uniform in {16, ..., 96} cells, density 5 or 10 per cell, rotation angle
+    90, 120 or 130 degrees, box seed 1000 + i; all drawn from
+    ``numpy.random.default_rng(seed)``.  Initial states are thermal (drawn on
+    the device from each box's seed)."""
+    rng = np.random.default_rng(seed)
+    edges = rng.integers(16, 97, n_boxes)
+    dens = rng.choice([5, 10], n_boxes)
+    angles = rng.choice([90.0, 120.0, 130.0], n_boxes)
+    return [dict(n=(int(e), int(e), int(e)), density=int(d), alpha_deg=float(a), seed=1000 + i)
+            for i, (e, d, a) in enumerate(zip(edges, dens, angles))]
+
+
 # Named workloads (sizes of the benchmark set-ups).  Each entry gives the
 # keyword arguments of the SRD parameters and of the solvent generator.
 WORKLOADS = {
@@ -95,4 +109,13 @@ WORKLOADS = {
                                        steps=500, n_chains=2000, chain_len=50,
                                        bead_mass=5.0, bond_k=1000.0, bond_r0=0.5,
                                        md_substeps=10),
+    # 64 boxes of ensemble() stepped together, against the same boxes stepped
+    # one after another
+    "srd-batch64-mixed": dict(kind="batch", n_boxes=64, ensemble_seed=4, dt=0.1, kT=1.0,
+                              thermostat=False, precision="mixed", steps=1000),
+    # Poisson arrivals of SRD jobs served by continuous batching
+    "srd-served-poisson": dict(kind="serve", n_jobs=2000, rate=20.0, jobs_seed=5, l_min=10,
+                               l_max=160, density=5.0, steps_min=100, steps_max=5000,
+                               alpha_deg=130.0, precision="mixed", sweep_rates=(5.0, 10.0, 15.0),
+                               sweep_jobs=300),
 }
