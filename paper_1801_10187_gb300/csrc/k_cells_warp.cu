@@ -18,11 +18,12 @@
 //   cell     lane c turns the sums of cell c into u, draws the axis (and with
 //            the thermostat, after the same kind of pass for the energy about
 //            u, the factor xi) and leaves them in shared memory
-//   pass 2   members in order across the lanes, two records in flight per
-//            lane: collide with the cell's parameters, stream, bin under the
-//            next shift, take a slot in the new row and write the record
-//            there; lanes bound for the same cell share one atomic on its
-//            count (match.any), which cuts the slot requests about threefold
+//   pass 2   members in order across the lanes, in chunks of three windows:
+//            the chunk's records are copied into shared memory asynchronously
+//            (all in flight at once), each is collided with its cell's
+//            parameters, streamed and binned under the next shift while its
+//            slot in the new row is requested (atomic on the row count), and
+//            the records are written once every request of the chunk is out
 // The parameters a member needs (time step, box, rotation, the thresholds of
 // the next grid shift, row pointers) are staged in shared memory when a block
 // meets a new box.  Members beyond the row capacity (overflow list) stay with the lane
@@ -45,6 +46,17 @@ constexpr int WARPS = BLOCK / 32;
 constexpr int MAP_MEMBERS = 640;  // members per warp with a byte owner map
 constexpr int STAGE = 256;        // member velocities staged per block of pass 1
 constexpr int STAGE_PAD = STAGE + STAGE / 32;
+constexpr int CHUNK = 3;          // windows of 32 members per chunk of pass 2
+
+// 16-byte asynchronous copy global -> shared (bypassing L1), and the wait for
+// all of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
 
 struct WarpShared {
   float4 prm[2][32];               // (u, xi), (axis, 0) per cell
@@ -53,7 +65,10 @@ struct WarpShared {
   int offs[33];                    // first member of each cell; offs[32] = members
   int pad_[3];
   unsigned char map[MAP_MEMBERS];  // owner lane of each member
-  float sv[3][STAGE_PAD];          // staged velocities (index j + j / 32)
+  union {
+    float sv[3][STAGE_PAD];        // pass 1: staged velocities (index j + j / 32)
+    float4 buf[CHUNK][32][2];      // pass 2: records of one chunk
+  };
 };
 
 // Shared memory of one block: the span parameters, then one area per warp;
@@ -440,66 +455,52 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         }
       }
     };
-    if (MODE == MODE_C) {
-      // collide in place, two records in flight per lane
-      for (int base = 0; base < N; base += 64) {
-        const int ma = base + lane, mb = base + 32 + lane;
-        float ra[3], wa[3], rb[3], wb[3];
-        uint32_t ta = 0u, tb = 0u;
-        int oa = 0, ob = 0;
-        R* pa = rows;
-        R* pb = rows;
-        if (ma < N) {
-          oa = owner_of(ma);
-          pa = member(ma, oa);
-          load_rec(pa, ra, wa, ta);
-        }
-        if (mb < N) {
-          ob = owner_of(mb);
-          pb = member(mb, ob);
-          load_rec(pb, rb, wb, tb);
-        }
-        if (ma < N) {
-          advance(ra, wa, oa);
-          store_rec(pa, ra, wa, ta);
-        }
-        if (mb < N) {
-          advance(rb, wb, ob);
-          store_rec(pb, rb, wb, tb);
+    // Chunks of CHUNK windows: (a) every record of the chunk is copied into
+    // shared memory by asynchronous copies (all in flight together, no
+    // registers held); (b) each is advanced and, in modes P and F, written
+    // back with its new cell while the slot request for it goes out; (c) once
+    // all slot requests of the chunk are out, the records are written to
+    // their rows.  One load latency and one slot latency per chunk.
+    for (int base = 0; base < N; base += 32 * CHUNK) {
+#pragma unroll
+      for (int w = 0; w < CHUNK; ++w) {
+        const int m = base + (w << 5) + lane;
+        if (m < N) {
+          const R* p = member(m, owner_of(m));
+          cp_async16(&W.buf[w][lane][0], p);
+          cp_async16(&W.buf[w][lane][1], reinterpret_cast<const float4*>(p) + 1);
         }
       }
-    } else {
-      // Slots in the new rows: the lanes of a window that go to the same cell
-      // take consecutive slots with one atomic, made by the first of them.
-      auto take_slot = [&](bool act, uint32_t c2) -> uint32_t {
-        const unsigned peers = __match_any_sync(FULL, act ? c2 : 0xFFFFFFFFu);
-        const int leader = __ffs(peers) - 1;
-        uint32_t base = 0u;
-        if (act && lane == leader) base = atomicAdd(&H.cnt_out[c2], (uint32_t)__popc(peers));
-        base = __shfl_sync(FULL, base, leader);
-        return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-      };
-      // two records in flight per lane
-      for (int base = 0; base < N; base += 64) {
-        const int ma = base + lane, mb = base + 32 + lane;
-        const bool acta = ma < N, actb = mb < N;
-        float ra[3], wa[3], rb[3], wb[3];
-        uint32_t ta = 0u, tb = 0u, ca = 0u, cb = 0u;
-        int oa = 0, ob = 0;
-        if (acta) {
-          oa = owner_of(ma);
-          load_rec(member(ma, oa), ra, wa, ta);
+      cp_async_wait_all();  // each lane reads back only its own copies
+      uint32_t slot[CHUNK];
+#pragma unroll
+      for (int w = 0; w < CHUNK; ++w) {
+        const int m = base + (w << 5) + lane;
+        slot[w] = 0u;
+        if (m < N) {
+          const int o = owner_of(m);
+          const float4 x = W.buf[w][lane][0], y = W.buf[w][lane][1];
+          float r[3] = {x.x, x.y, x.z}, v[3] = {x.w, y.x, y.y};
+          const uint32_t c2 = advance(r, v, o);
+          if (MODE == MODE_C) {
+            store_rec(member(m, o), r, v, __float_as_uint(y.z));
+          } else {
+            W.buf[w][lane][0] = make_float4(r[0], r[1], r[2], v[0]);
+            W.buf[w][lane][1] = make_float4(v[1], v[2], y.z, __uint_as_float(c2));
+            slot[w] = atomicAdd(&H.cnt_out[c2], 1u);
+          }
         }
-        if (actb) {
-          ob = owner_of(mb);
-          load_rec(member(mb, ob), rb, wb, tb);
+      }
+      if (MODE != MODE_C) {
+#pragma unroll
+        for (int w = 0; w < CHUNK; ++w) {
+          const int m = base + (w << 5) + lane;
+          if (m < N) {
+            const float4 x = W.buf[w][lane][0], y = W.buf[w][lane][1];
+            const float r[3] = {x.x, x.y, x.z}, v[3] = {x.w, y.x, y.y};
+            emit(r, v, __float_as_uint(y.z), __float_as_uint(y.w), slot[w]);
+          }
         }
-        if (acta) ca = advance(ra, wa, oa);
-        if (actb) cb = advance(rb, wb, ob);
-        const uint32_t sa = take_slot(acta, ca);
-        const uint32_t sb = take_slot(actb, cb);
-        if (acta) emit(ra, wa, ta, ca, sa);
-        if (actb) emit(rb, wb, tb, cb, sb);
       }
     }
     if (has_ovf) {
