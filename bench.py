@@ -182,8 +182,9 @@ def oracle_rate(cfg, budget_s, steps=None, warmup=0):
 
 # ------------------------------------------------------------------ traffic record
 def kernel_traffic(kernel, workload):
-    """dram bytes per launch from a committed ncu summary, if it was taken on
-    the current source of that kernel (else None)."""
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary
+    record, if it was taken on the current sources of that kernel (their
+    combined hash matches), else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -192,12 +193,17 @@ def kernel_traffic(kernel, workload):
     ent = rec.get(f"{kernel}/{workload}")
     if not ent:
         return None
-    src = os.path.join(ROOT, ent["source"])
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
-    if h != ent.get("source_sha256_16"):
+    if sources_hash(ent["sources"]) != ent.get("sources_sha256_16"):
         return None
     return ent["dram_bytes_per_launch"] * ent.get("scale_to_workload", 1.0)
+
+
+def sources_hash(paths):
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------------ main

@@ -17,14 +17,14 @@ __device__ __forceinline__ void load_rec(const RecF* p, float r[3], float v[3], 
   float t;
   [[maybe_unused]] float pad;
   asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(v[0]), "=f"(v[1]), "=f"(v[2]),
-                 "=f"(t), "=f"(pad)
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(t), "=f"(r[0]), "=f"(r[1]),
+                 "=f"(r[2]), "=f"(pad)
                : "l"(p));
   tag = __float_as_uint(t);
 }
 __device__ __forceinline__ void store_rec(RecF* p, const float r[3], const float v[3], uint32_t tag) {
-  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(r[0]),
-               "f"(r[1]), "f"(r[2]), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(__uint_as_float(tag)),
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]),
+               "f"(v[1]), "f"(v[2]), "f"(__uint_as_float(tag)), "f"(r[0]), "f"(r[1]), "f"(r[2]),
                "f"(0.0f)
                : "memory");
 }
@@ -45,8 +45,7 @@ __device__ __forceinline__ void store_rec(RecD* p, const double r[3], const doub
 }
 __device__ __forceinline__ void load_v(const RecF* p, float v[3]) {
   const float4 a = reinterpret_cast<const float4*>(p)[0];
-  const float2 b = reinterpret_cast<const float2*>(p)[2];
-  v[0] = a.w; v[1] = b.x; v[2] = b.y;
+  v[0] = a.x; v[1] = a.y; v[2] = a.z;
 }
 __device__ __forceinline__ void load_v(const RecD* p, double v[3]) {
   const double2 b = reinterpret_cast<const double2*>(p)[1];

@@ -67,7 +67,7 @@ struct WarpShared {
   unsigned char map[MAP_MEMBERS];  // owner lane of each member
   union {
     float sv[3][STAGE_PAD];        // pass 1: staged velocities (index j + j / 32)
-    float4 buf[CHUNK][32][2];      // pass 2: records of one chunk
+    float4 buf[CHUNK][2][32];      // pass 2: records of one chunk (two halves)
   };
 };
 
@@ -222,25 +222,20 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
     // member order (neighbouring lanes, neighbouring records).
     auto stage = [&](int sbase, int cnt) {
       for (int j0 = 0; j0 < cnt; j0 += 128) {  // four windows of loads in flight
-        float a[4];
-        float2 b[4];
+        float4 a[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = j0 + (u << 5) + lane;
-          if (j < cnt) {
-            const float* p = reinterpret_cast<const float*>(member(sbase + j, owner_of(sbase + j)));
-            a[u] = p[3];
-            b[u] = *reinterpret_cast<const float2*>(p + 4);
-          }
+          if (j < cnt) a[u] = *reinterpret_cast<const float4*>(member(sbase + j, owner_of(sbase + j)));
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = j0 + (u << 5) + lane;
           if (j < cnt) {
             const int js = j + (j >> 5);
-            W.sv[0][js] = a[u];
-            W.sv[1][js] = b[u].x;
-            W.sv[2][js] = b[u].y;
+            W.sv[0][js] = a[u].x;
+            W.sv[1][js] = a[u].y;
+            W.sv[2][js] = a[u].z;
           }
         }
       }
@@ -467,8 +462,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         const int m = base + (w << 5) + lane;
         if (m < N) {
           const R* p = member(m, owner_of(m));
-          cp_async16(&W.buf[w][lane][0], p);
-          cp_async16(&W.buf[w][lane][1], reinterpret_cast<const float4*>(p) + 1);
+          cp_async16(&W.buf[w][0][lane], p);
+          cp_async16(&W.buf[w][1][lane], reinterpret_cast<const float4*>(p) + 1);
         }
       }
       cp_async_wait_all();  // each lane reads back only its own copies
@@ -479,14 +474,14 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         slot[w] = 0u;
         if (m < N) {
           const int o = owner_of(m);
-          const float4 x = W.buf[w][lane][0], y = W.buf[w][lane][1];
-          float r[3] = {x.x, x.y, x.z}, v[3] = {x.w, y.x, y.y};
+          const float4 x = W.buf[w][0][lane], y = W.buf[w][1][lane];  // (v, tag), (r, pad)
+          float v[3] = {x.x, x.y, x.z}, r[3] = {y.x, y.y, y.z};
           const uint32_t c2 = advance(r, v, o);
           if (MODE == MODE_C) {
-            store_rec(member(m, o), r, v, __float_as_uint(y.z));
+            store_rec(member(m, o), r, v, __float_as_uint(x.w));
           } else {
-            W.buf[w][lane][0] = make_float4(r[0], r[1], r[2], v[0]);
-            W.buf[w][lane][1] = make_float4(v[1], v[2], y.z, __uint_as_float(c2));
+            W.buf[w][0][lane] = make_float4(v[0], v[1], v[2], x.w);
+            W.buf[w][1][lane] = make_float4(r[0], r[1], r[2], __uint_as_float(c2));
             slot[w] = atomicAdd(&H.cnt_out[c2], 1u);
           }
         }
@@ -496,9 +491,9 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         for (int w = 0; w < CHUNK; ++w) {
           const int m = base + (w << 5) + lane;
           if (m < N) {
-            const float4 x = W.buf[w][lane][0], y = W.buf[w][lane][1];
-            const float r[3] = {x.x, x.y, x.z}, v[3] = {x.w, y.x, y.y};
-            emit(r, v, __float_as_uint(y.z), __float_as_uint(y.w), slot[w]);
+            const float4 x = W.buf[w][0][lane], y = W.buf[w][1][lane];
+            const float v[3] = {x.x, x.y, x.z}, r[3] = {y.x, y.y, y.z};
+            emit(r, v, __float_as_uint(x.w), __float_as_uint(y.w), slot[w]);
           }
         }
       }

@@ -41,10 +41,14 @@ constexpr int ERR_OVERFLOW_CAP = 4;  // overflow list full (cannot happen: it ho
 // Passes of the fused step kernel.
 enum { MODE_P = 0, MODE_F = 1, MODE_C = 2 };
 
-// One particle (mixed model: 32 bytes, FP64: 64 bytes).
+// One particle (mixed model: 32 bytes, FP64: 64 bytes).  The mixed record
+// keeps the velocity in its first 16 bytes, so the cell sums read one
+// aligned 16-byte word per particle.
 struct __align__(16) RecF {
-  float x, y, z, vx, vy, vz;
-  uint32_t tag, pad;
+  float vx, vy, vz;
+  uint32_t tag;
+  float x, y, z;
+  uint32_t pad;
 };
 struct __align__(16) RecD {
   double x, y, z, vx, vy, vz;
