@@ -309,8 +309,8 @@ def main():
     dom = "fused_step"
     dom_ms = phases[dom]
     achieved = step_bytes * s.pos.shape[0] / (dom_ms * 1e-3) / 1e9
-    # the warp-spread kernel runs mixed-model boxes without walls or solute
-    kname = "k_cells_warp" if cfg["precision"] == "mixed" and not cfg.get("n_chains") else "k_cells"
+    # the warp-spread kernel runs mixed-model boxes without walls
+    kname = "k_cells_warp" if cfg["precision"] == "mixed" else "k_cells"
     traffic = kernel_traffic(kname, args.workload)
     roofline = {"bound": "hbm", "kernel": f"{kname} (collide t + stream/bin t+1)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

@@ -137,9 +137,9 @@ struct Engine {
   BoxDev* d_boxes = nullptr;
   int n_records = 0;
   // per kernel variant: thermostat (1) | walls or beads (2) | warp-spread members (4);
-  // for the warp-spread kernel bit 2 means a nonzero body force instead
-  int2* d_spans[8] = {};
-  int n_spans[8] = {};
+  // for the warp-spread kernel bit 2 means a nonzero body force and bit 8 beads
+  int2* d_spans[16] = {};
+  int n_spans[16] = {};
   ScanSeg* d_bsegs = nullptr;
   int2* d_bstiles = nullptr;
   int n_bstiles = 0;
@@ -154,7 +154,7 @@ struct Engine {
   int* d_err = nullptr;
   double* d_partials = nullptr;
   bool any_beads = false;
-  int cells_bps[3][8] = {};
+  int cells_bps[3][16] = {};
 
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // MODE_P, MODE_F, MODE_C
   bool tables_ok = false;
@@ -173,9 +173,14 @@ struct Engine {
       own_stream = true;
     }
     for (int m = 0; m < 3; ++m)
-      for (int v = 0; v < 8; ++v) {
-        if (v & 4) cells_bps[m][v] = mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, m) : 1;
-        else cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
+      for (int v = 0; v < 16; ++v) {
+        if (v & 4)
+          cells_bps[m][v] =
+              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, m) : 1;
+        else if (v < 4)
+          cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
+        else
+          cells_bps[m][v] = 1;
         if (cells_bps[m][v] < 1) cells_bps[m][v] = 1;
       }
     CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
@@ -194,7 +199,7 @@ struct Engine {
     void* ptrs[] = {d_boxes, d_bsegs, d_bstiles, d_btiles, d_mdtiles, d_tsum, d_gscan, d_toff};
     for (void* q : ptrs)
       if (q) cudaFree(q);
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < 16; ++v) {
       if (d_spans[v]) cudaFree(d_spans[v]);
       d_spans[v] = nullptr;
       n_spans[v] = 0;
@@ -290,7 +295,7 @@ struct Engine {
     tables_ok = true;
     if (live.empty()) return MPCD_OK;
     std::vector<BoxDev> rec;
-    std::vector<int2> sp[8], bst, bt, mt;
+    std::vector<int2> sp[16], bst, bt, mt;
     std::vector<ScanSeg> bseg;
     any_beads = false;
     int max_cl = 1;
@@ -304,10 +309,10 @@ struct Engine {
       rec.push_back(b->d);
       const BoxDev& d = b->d;
       int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0);
-      if (mixed && !(variant & 2) && d.K <= WARP_MAX_K &&
+      if (mixed && !d.walls && d.K <= WARP_MAX_K &&
           std::max(d.n[0], std::max(d.n[1], d.n[2])) < (1 << 22)) {
         const bool force = d.g[0] != 0.0 || d.g[1] != 0.0 || d.g[2] != 0.0;
-        variant = 4 | (d.thermostat ? 1 : 0) | (force ? 2 : 0);
+        variant = 4 | (d.thermostat ? 1 : 0) | (force ? 2 : 0) | (d.nbead > 0 ? 8 : 0);
       }
       for (int c0 = 0; c0 < d.ncells; c0 += BLOCK) sp[variant].push_back(make_int2((int)i, c0));
       if (d.nbead > 0) {
@@ -330,7 +335,7 @@ struct Engine {
       return MPCD_OK;
     };
     if ((rc = up(rec, d_boxes, &n_records))) return rc;
-    for (int v = 0; v < 8; ++v)
+    for (int v = 0; v < 16; ++v)
       if ((rc = up(sp[v], d_spans[v], &n_spans[v]))) return rc;
     if ((rc = up(bseg, d_bsegs, nullptr))) return rc;
     if ((rc = up(bst, d_bstiles, &n_bstiles))) return rc;
@@ -351,11 +356,12 @@ struct Engine {
   }
 
   void launch_cells_all(int mode) {
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < 16; ++v) {
+      if (n_spans[v] == 0) continue;
       const int grid = grid_for(n_spans[v], cells_bps[mode][v]);
       if (v & 4)
-        launch_cells_warp((v & 1) != 0, (v & 2) != 0, mode, d_boxes, d_spans[v], n_spans[v], grid,
-                          d_err, stream);
+        launch_cells_warp((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, mode, d_boxes, d_spans[v],
+                          n_spans[v], grid, d_err, stream);
       else
         launch_cells(mixed, v, mode, d_boxes, d_spans[v], n_spans[v], grid, d_err, stream);
     }

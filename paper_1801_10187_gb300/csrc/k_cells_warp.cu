@@ -4,7 +4,7 @@
 // Sec. 3.6 rotation and thermostat, algorithm "SRD collision rule").
 //
 // Same modes, records and results as k_cells (one thread per cell), for boxes
-// without walls or solute.  A warp owns 32 consecutive cells.  Their row
+// without walls (solute beads allowed).  A warp owns 32 consecutive cells.  Their row
 // members are numbered 0 .. N-1 in cell order (a warp prefix sum of the row
 // counts); a byte map gives each member's cell.
 //   pass 1   the velocities of up to 256 members are read in member order
@@ -133,7 +133,7 @@ __device__ __forceinline__ float wrap_fast(float x, float L) {
 
 }  // namespace
 
-template <bool THERMO, int MODE, bool FORCE>
+template <bool THERMO, int MODE, bool FORCE, bool BEADS>
 __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restrict__ boxes,
                                                          const int2* __restrict__ spans,
                                                          int nspans, int* err) {
@@ -300,8 +300,26 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
       const bool exact64 = __any_sync(FULL, slow);  // a velocity of 1024 or more
 
       // ---- per cell: u (Sec. 3.5), then the energy about u, axis and xi ----
+      // Solute beads join their cell's collision with mass M (Sec. 3.6); the
+      // beads of these 32 cells form one bead group (32-cell groups).
+      int gb0 = 0, gnb = 0, nb = 0;
+      long long X[3] = {0, 0, 0};
+      if (BEADS) {
+        const int g = c0 / B.tc;
+        gb0 = (int)B.bstart[g];
+        gnb = (int)B.bstart[g + 1] - gb0;
+        for (int j = 0; j < gnb; ++j) {
+          const int b = (int)B.border[gb0 + j];
+          if (B.bcell[b] == cell) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) X[q] += __double2ll_rn((B.Mb * B.svel[3 * b + q]) * 4294967296.0);
+            ++nb;
+          }
+        }
+      }
+      const bool occupied = n > 0 || nb > 0;
       float u[3] = {0.0f, 0.0f, 0.0f};
-      if (n > 0) {
+      if (occupied) {
         long long Q[3] = {0, 0, 0};
         if (exact64)
           for (int k = 0; k < nrow; ++k) {
@@ -318,11 +336,13 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
 #pragma unroll
               for (int q = 0; q < 3; ++q) Q[q] += fix32_rne(w[q]);
             }
-        const float M = H.m * small_to_float((int)n);
+        float M = H.m * small_to_float((int)n);
+        if (BEADS) M = M + (small_to_float(nb) * B.Mb_f + 0.0f * H.m);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          const float P = H.m * (exact64 ? i64_to_float(Q[q])
-                                         : split_sum_to_float(W.h[q][lane], W.l[q][lane], Q[q]));
+          float P = H.m * (exact64 ? i64_to_float(Q[q])
+                                   : split_sum_to_float(W.h[q][lane], W.l[q][lane], Q[q]));
+          if (BEADS) P = P + i64_to_float(X[q]);
           u[q] = (P * 0x1p-32f) / M;
         }
         W.prm[0][lane] = make_float4(u[0], u[1], u[2], 1.0f);
@@ -359,8 +379,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
           __syncwarp();
         }
         const bool exact64_e = __any_sync(FULL, slow_e);
-        if (n > 0) {
-          long long Es = 0;
+        if (occupied) {
+          long long Es = 0, Ex = 0;
           auto add_energy = [&](const R* p) {
             float w[3];
             load_v(p, w);
@@ -372,22 +392,52 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
           if (has_ovf)
             for (uint32_t j = 0; j < novf; ++j)
               if (ovf_cell[j] == (uint32_t)cell) add_energy(ovf + j);
-          // Eq. thermo: E_k about u, E^ ~ Gamma(3(n-1)/2, kT), xi = sqrt(E^/E_k)
-          const float E = H.m * (exact64_e ? i64_to_float(Es)
-                                           : split_sum_to_float(W.h[0][lane], W.l[0][lane], Es));
+          if (BEADS)
+            for (int j = 0; j < gnb; ++j) {
+              const int b = (int)B.border[gb0 + j];
+              if (B.bcell[b] == cell) {
+                const double d0 = B.svel[3 * b] - (double)u[0], d1 = B.svel[3 * b + 1] - (double)u[1],
+                             d2 = B.svel[3 * b + 2] - (double)u[2];
+                Ex += __double2ll_rn((B.Mb * (d0 * d0 + d1 * d1 + d2 * d2)) * 4294967296.0);
+              }
+            }
+          // Eq. thermo: E_k about u, E^ ~ Gamma(3(N_c-1)/2, kT), xi = sqrt(E^/E_k)
+          float E = H.m * (exact64_e ? i64_to_float(Es)
+                                     : split_sum_to_float(W.h[0][lane], W.l[0][lane], Es));
+          if (BEADS) E = E + i64_to_float(Ex);
           const float Ek = (0.5f * E) * 0x1p-32f;
-          if (n >= 2 && Ek > 0.0f) {
+          const int nc = (int)n + nb;
+          if (nc >= 2 && Ek > 0.0f) {
             float ehat;
-            if (gamma_draw(B, t, (uint32_t)cell, (int)n, ehat)) xi = sqrtf(ehat / Ek);
+            if (gamma_draw(B, t, (uint32_t)cell, nc, ehat)) xi = sqrtf(ehat / Ek);
             else atomicOr(err, ERR_GAMMA_CAP);
           }
         }
       }
-      if (n > 0) {
+      if (occupied) {
         float ax[3];
         axis_of(B, t, (uint32_t)cell, ax);  // Sec. 3.6
         W.prm[0][lane] = make_float4(u[0], u[1], u[2], xi);
         W.prm[1][lane] = make_float4(ax[0], ax[1], ax[2], 0.0f);
+        if (BEADS && nb > 0) {
+          CellParams<float> prm;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            prm.u[q] = u[q];
+            prm.n[q] = ax[q];
+          }
+          prm.xi = xi;
+          for (int j = 0; j < gnb; ++j) {
+            const int b = (int)B.border[gb0 + j];
+            if (B.bcell[b] == cell) {
+              double w[3] = {B.svel[3 * b], B.svel[3 * b + 1], B.svel[3 * b + 2]};
+              collide_bead<true>(B, prm, w, THERMO);
+              B.svel[3 * b] = w[0];
+              B.svel[3 * b + 1] = w[1];
+              B.svel[3 * b + 2] = w[2];
+            }
+          }
+        }
       }
       __syncwarp();
     }
@@ -513,36 +563,42 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
   }
 }
 
-template <bool TH, int MODE, bool FO>
+template <bool TH, int MODE, bool FO, bool BE>
 static void* warp_fn() {
-  return (void*)k_cells_warp<TH, MODE, FO>;
+  return (void*)k_cells_warp<TH, MODE, FO, BE>;
+}
+
+template <int MODE, bool BE>
+static void* warp_variant_mb(bool thermo, bool force) {
+  if (thermo) return force ? warp_fn<true, MODE, true, BE>() : warp_fn<true, MODE, false, BE>();
+  return force ? warp_fn<false, MODE, true, BE>() : warp_fn<false, MODE, false, BE>();
 }
 
 template <int MODE>
-static void* warp_variant_mode(bool thermo, bool force) {
-  if (thermo) return force ? warp_fn<true, MODE, true>() : warp_fn<true, MODE, false>();
-  return force ? warp_fn<false, MODE, true>() : warp_fn<false, MODE, false>();
+static void* warp_variant_mode(bool thermo, bool force, bool beads) {
+  return beads ? warp_variant_mb<MODE, true>(thermo, force) : warp_variant_mb<MODE, false>(thermo, force);
 }
 
-static void* warp_variant(bool thermo, bool force, int mode) {
-  if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force);
-  if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force);
-  return warp_variant_mode<MODE_C>(thermo, force);
+static void* warp_variant(bool thermo, bool force, bool beads, int mode) {
+  if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force, beads);
+  if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force, beads);
+  return warp_variant_mode<MODE_C>(thermo, force, beads);
 }
 
-int cells_warp_blocks_per_sm(bool thermo, bool force, int mode) {
-  const void* fn = warp_variant(thermo, force, mode);
+int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, int mode) {
+  const void* fn = warp_variant(thermo, force, beads, mode);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BLOCK_SMEM);
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, BLOCK_SMEM);
   return nb;
 }
 
-void launch_cells_warp(bool thermo, bool force, int mode, const BoxDev* boxes, const int2* spans,
-                       int nspans, int grid, int* err, cudaStream_t s) {
+void launch_cells_warp(bool thermo, bool force, bool beads, int mode, const BoxDev* boxes,
+                       const int2* spans, int nspans, int grid, int* err, cudaStream_t s) {
   if (nspans <= 0) return;
   void* args[] = {(void*)&boxes, (void*)&spans, (void*)&nspans, (void*)&err};
-  cudaLaunchKernel(warp_variant(thermo, force, mode), dim3(grid), dim3(BLOCK), args, BLOCK_SMEM, s);
+  cudaLaunchKernel(warp_variant(thermo, force, beads, mode), dim3(grid), dim3(BLOCK), args,
+                   BLOCK_SMEM, s);
 }
 
 }  // namespace mpcd

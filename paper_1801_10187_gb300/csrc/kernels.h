@@ -13,13 +13,14 @@ namespace mpcd {
 int cells_blocks_per_sm(bool mixed, int variant, int mode);
 void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const int2* spans,
                   int nspans, int grid, int* err, cudaStream_t s);
-// The same step for mixed-model boxes without walls or beads, members spread
-// over the lanes of a warp (k_cells_warp.cu); valid for row capacities up to
-// WARP_MAX_K and boxes below 2^22 cells per axis.  force: nonzero body force.
+// The same step for mixed-model boxes without walls, members spread over the
+// lanes of a warp (k_cells_warp.cu); valid for row capacities up to
+// WARP_MAX_K and boxes below 2^22 cells per axis.  force: nonzero body force;
+// beads: the box has solute beads.
 constexpr int WARP_MAX_K = 448;
-int cells_warp_blocks_per_sm(bool thermo, bool force, int mode);
-void launch_cells_warp(bool thermo, bool force, int mode, const BoxDev* boxes, const int2* spans,
-                       int nspans, int grid, int* err, cudaStream_t s);
+int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, int mode);
+void launch_cells_warp(bool thermo, bool force, bool beads, int mode, const BoxDev* boxes,
+                       const int2* spans, int nspans, int grid, int* err, cudaStream_t s);
 // Place n particles (device arrays of float (mixed) or double, n x 3) in the
 // current rows of a box whose counts are zero.
 void launch_load(bool mixed, const BoxDev* box, const void* pos, const void* vel, int n, int* err,
