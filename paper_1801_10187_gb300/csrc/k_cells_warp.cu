@@ -517,11 +517,16 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         }
       }
       cp_async_wait_all();  // each lane reads back only its own copies
-      uint32_t slot[CHUNK];
+      // Slots: the lanes of a window bound for the same cell share one atomic
+      // (made by the first of them) and take consecutive slots, so their
+      // records land side by side.  The atomic's result is read only when
+      // the chunk is written.
+      uint32_t sbase[CHUNK];
+      int lr[CHUNK];  // leader lane | rank << 8
 #pragma unroll
       for (int w = 0; w < CHUNK; ++w) {
         const int m = base + (w << 5) + lane;
-        slot[w] = 0u;
+        uint32_t key = 0xFFFFFFFFu;
         if (m < N) {
           const int o = owner_of(m);
           const float4 x = W.buf[w][0][lane], y = W.buf[w][1][lane];  // (v, tag), (r, pad)
@@ -532,18 +537,27 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
           } else {
             W.buf[w][0][lane] = make_float4(v[0], v[1], v[2], x.w);
             W.buf[w][1][lane] = make_float4(r[0], r[1], r[2], __uint_as_float(c2));
-            slot[w] = atomicAdd(&H.cnt_out[c2], 1u);
+            key = c2;
           }
+        }
+        if (MODE != MODE_C) {
+          const unsigned peers = __match_any_sync(FULL, key);
+          const int leader = __ffs(peers) - 1;
+          sbase[w] = 0u;
+          if (key != 0xFFFFFFFFu && lane == leader)
+            sbase[w] = atomicAdd(&H.cnt_out[key], (uint32_t)__popc(peers));
+          lr[w] = leader | (__popc(peers & ((1u << lane) - 1u)) << 8);
         }
       }
       if (MODE != MODE_C) {
 #pragma unroll
         for (int w = 0; w < CHUNK; ++w) {
           const int m = base + (w << 5) + lane;
+          const uint32_t slot = __shfl_sync(FULL, sbase[w], lr[w] & 255) + (uint32_t)(lr[w] >> 8);
           if (m < N) {
             const float4 x = W.buf[w][0][lane], y = W.buf[w][1][lane];
             const float v[3] = {x.x, x.y, x.z}, r[3] = {y.x, y.y, y.z};
-            emit(r, v, __float_as_uint(x.w), __float_as_uint(y.w), slot[w]);
+            emit(r, v, __float_as_uint(x.w), __float_as_uint(y.w), slot);
           }
         }
       }
