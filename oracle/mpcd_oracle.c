@@ -194,28 +194,35 @@ int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, 
     double dd = (double)d, cd = (double)c;
     float kTf = (float)kT;
     for (uint32_t j = 0; j < 64; ++j) {
-      uint32_t wa[4], wb[4];
+      /* Attempt j: block A = counter (cell, 1 + 2j).  Its words 0, 2 and 1 are
+       * the high words of U1, U2 and U3 (the FP64 model takes the low words
+       * from block B), so the mixed model needs only block A. */
+      uint32_t wa[4];
       draw4(seed, ORACLE_PURPOSE_THERMO, cell, 1u + 2u * j, t, wa);
-      draw4(seed, ORACLE_PURPOSE_THERMO, cell, 2u + 2u * j, t, wb);
-      /* 1 - U1 from the exact integer 2^32 - w, cos(2 pi U2) by quadrants,
-       * U3 = w / 2^32: the high words of the double-precision uniforms. */
       float e1 = (float)(4294967296LL - (int64_t)wa[0]) * 0x1p-32f;
-      float U3 = (float)wb[0] * 0x1p-32f;
+      float U3 = (float)wa[1] * 0x1p-32f;
       float c2, s2;
       cos_sin_turn_f(wa[2], &c2, &s2);
       float x = sqrtf(-2.0f * log_series_f(e1)) * c2;
       float t1 = 1.0f + c * x;
       if (!(t1 > 0.0f)) continue;
       float v = t1 * t1 * t1;
+      /* Squeeze of Marsaglia and Tsang (2000): U3 < 1 - 0.0331 x^4 lies inside
+       * the acceptance region, so it accepts without the logarithms. */
+      float x2 = x * x;
+      if (U3 < 1.0f - 0.0331f * (x2 * x2)) {
+        *ehat = (double)(d * v * kTf);
+        return 0;
+      }
       float lhs = log_series_f(U3);
-      float rhs = 0.5f * (x * x) + d - d * v + d * log_series_f(v);
+      float rhs = 0.5f * x2 + d - d * v + d * log_series_f(v);
       float diff = lhs - rhs;
       int accept;
       if (fabsf(diff) > 1e-3f * (1.0f + d)) {
         accept = diff < 0.0f;
       } else {
         /* Too close to the acceptance boundary for float rounding to decide:
-         * decide in double from the same uniforms. */
+         * decide in double from the same high words. */
         double xd = sqrt(-2.0 * log((double)e1)) * cos(TWO_PI * ((double)wa[2] * 0x1p-32));
         double td = 1.0 + cd * xd;
         if (!(td > 0.0)) continue;
@@ -236,12 +243,15 @@ int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, 
     uint32_t wa[4], wb[4];
     draw4(seed, ORACLE_PURPOSE_THERMO, cell, 1u + 2u * j, t, wa);
     draw4(seed, ORACLE_PURPOSE_THERMO, cell, 2u + 2u * j, t, wb);
-    double U1 = u01_53(wa[0], wa[1]), U2 = u01_53(wa[2], wa[3]), U3 = u01_53(wb[0], wb[1]);
+    /* 53-bit uniforms: high words from block A (as in the mixed model), low
+     * words from block B. */
+    double U1 = u01_53(wa[0], wb[0]), U2 = u01_53(wa[2], wb[2]), U3 = u01_53(wa[1], wb[1]);
     double x = sqrt(-2.0 * log(1.0 - U1)) * cos(TWO_PI * U2);
     double t1 = 1.0 + c * x;
     if (!(t1 > 0.0)) continue;
     double v = t1 * t1 * t1;
-    if (log(U3) < 0.5 * x * x + d - d * v + d * log(v)) {
+    double x2 = x * x;
+    if (U3 < 1.0 - 0.0331 * (x2 * x2) || log(U3) < 0.5 * x2 + d - d * v + d * log(v)) {
       *ehat = d * v * kT;
       return 0;
     }

@@ -81,8 +81,11 @@ void oracle_shift(uint64_t seed, uint64_t t, double s[3]);
 void oracle_axis(uint64_t seed, uint64_t t, uint32_t cell, int32_t precision, double n[3]);
 
 /* Maxwell-Boltzmann kinetic-energy draw for a cell with nc >= 2 members:
- * Gamma(3(nc-1)/2, kT) by Marsaglia-Tsang.  Returns 0, or -4 if 64 attempts
- * were all rejected. */
+ * Gamma(3(nc-1)/2, kT) by Marsaglia-Tsang with its squeeze.  Attempt j reads
+ * Philox block A = counter (cell, 1 + 2j): words 0, 2, 1 are the high words
+ * of the uniforms U1, U2, U3 (Box-Muller from U1, U2; acceptance from U3);
+ * the FP64 model takes their low words from block B = (cell, 2 + 2j).
+ * Returns 0, or -4 if 64 attempts were all rejected. */
 int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc,
                           double kT, int32_t precision, double* ehat);
 
