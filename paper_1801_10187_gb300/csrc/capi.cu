@@ -76,7 +76,8 @@ size_t footprint_bytes(const mpcd_params& p, int64_t nsol, int64_t nbead) {
   b += 2 * (size_t)std::max<int64_t>(nsol, 1) * (rec_size(mixed) + 4);     // overflow lists
   b += (size_t)nsol * 6 * elem_size(mixed);                               // staging (r, v)
   if (nbead > 0) {
-    b += (size_t)nbead * (6 * sizeof(double) + sizeof(int32_t) + sizeof(uint64_t) + sizeof(uint32_t));
+    b += (size_t)nbead * (9 * sizeof(double) + 2 * sizeof(int32_t) + sizeof(uint64_t) +
+                          sizeof(uint32_t));
     b += (size_t)ng * sizeof(uint32_t) + (size_t)(ng + 1) * sizeof(uint32_t);
   }
   return b;
@@ -580,6 +581,8 @@ struct Engine {
       if ((rc = alloc(b, d.bcell, (size_t)nbead))) return rc;
       if ((rc = alloc(b, d.bkey, (size_t)nbead))) return rc;
       if ((rc = alloc(b, d.border, (size_t)nbead))) return rc;
+      if ((rc = alloc(b, d.bgc, (size_t)nbead))) return rc;
+      if ((rc = alloc(b, d.bgv, (size_t)nbead * 3))) return rc;
       if ((rc = alloc(b, d.bcount, (size_t)d.nctiles))) return rc;
       if ((rc = alloc(b, d.bstart, (size_t)d.nctiles + 1))) return rc;
       CUDA_TRY(cudaMemsetAsync(d.bcount, 0, sizeof(uint32_t) * d.nctiles, stream));

@@ -183,39 +183,52 @@ __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, u
 
 // ---------------------------------------------------------------------------
 // Eq. (thermo) / Sec. 3.6: E^ ~ Gamma(3(Nc-1)/2, kT) by Marsaglia-Tsang with a
-// Box-Muller normal; attempt j uses counters (cell, 1+2j) and (cell, 2+2j).
-// The float version settles acceptances within 1e-3 (1 + d) of the boundary
-// in double from the same uniforms.  Returns false after 64 rejections.
+// Box-Muller normal and the squeeze U3 < 1 - 0.0331 x^4 (inside the acceptance
+// region, so it accepts without logarithms).  Attempt j reads Philox block
+// A = counter (cell, 1 + 2j): words 0, 2, 1 are the high words of U1, U2, U3;
+// the FP64 sampler takes the low words from block B = (cell, 2 + 2j).  The
+// float version settles acceptances within 1e-3 (1 + d) of the boundary in
+// double from the same words.  Returns false after 64 rejections.
 // ---------------------------------------------------------------------------
+static __device__ __noinline__ bool gamma_accept_double(float d, float c, uint32_t w0, uint32_t w2,
+                                                 float U3, bool& ok) {
+  const double xd = sqrt(-2.0 * log((double)comp_word_to_float(w0) * 0x1p-32)) *
+                    cos(kTwoPi * ((double)w2 * 0x1p-32));
+  const double td = 1.0 + (double)c * xd;
+  ok = td > 0.0;
+  if (!ok) return false;
+  const double vd = td * td * td, dd = (double)d;
+  return log((double)U3) < 0.5 * xd * xd + dd - dd * vd + dd * log(vd);
+}
+
 __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
-                           float& ehat) {
+                                  float& ehat) {
   const float kk = 1.5f * small_to_float(nc - 1);
   const float d = kk - 1.0f / 3.0f;
   const float c = 1.0f / sqrtf(9.0f * d);
-  const double dd = (double)d, cd = (double)c;
   for (uint32_t j = 0; j < 64u; ++j) {
     const uint4 wa = draw(B, PURPOSE_THERMO, cell, 1u + 2u * j, t);
-    const uint4 wb = draw(B, PURPOSE_THERMO, cell, 2u + 2u * j, t);
     const float e1 = comp_word_to_float(wa.x) * 0x1p-32f;
-    const float U3 = word_to_float(wb.x) * 0x1p-32f;
+    const float U3 = word_to_float(wa.y) * 0x1p-32f;
     float c2, s2;
     turn_cos_sin(wa.z, c2, s2);
     const float x = sqrtf(-2.0f * series_log(e1)) * c2;
     const float t1 = 1.0f + c * x;
     if (!(t1 > 0.0f)) continue;
     const float v = t1 * t1 * t1;
-    const float lhs = series_log(U3);
-    const float rhs = 0.5f * (x * x) + d - d * v + d * series_log(v);
-    const float diff = lhs - rhs;
-    bool accept;
-    if (fabsf(diff) > 1e-3f * (1.0f + d)) {
-      accept = diff < 0.0f;
-    } else {
-      const double xd = sqrt(-2.0 * log((double)e1)) * cos(kTwoPi * ((double)wa.z * 0x1p-32));
-      const double td = 1.0 + cd * xd;
-      if (!(td > 0.0)) continue;
-      const double vd = td * td * td;
-      accept = log((double)U3) < 0.5 * xd * xd + dd - dd * vd + dd * log(vd);
+    const float x2 = x * x;
+    bool accept = U3 < 1.0f - 0.0331f * (x2 * x2);
+    if (!accept) {
+      const float lhs = series_log(U3);
+      const float rhs = 0.5f * x2 + d - d * v + d * series_log(v);
+      const float diff = lhs - rhs;
+      if (fabsf(diff) > 1e-3f * (1.0f + d)) {
+        accept = diff < 0.0f;
+      } else {
+        bool ok;
+        accept = gamma_accept_double(d, c, wa.x, wa.z, U3, ok);
+        if (!ok) continue;
+      }
     }
     if (accept) {
       ehat = d * v * B.kT_f;
@@ -226,19 +239,20 @@ __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_
 }
 
 __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
-                           double& ehat) {
+                                  double& ehat) {
   const double kk = 1.5 * (double)(nc - 1);
   const double d = kk - 1.0 / 3.0;
   const double c = 1.0 / sqrt(9.0 * d);
   for (uint32_t j = 0; j < 64u; ++j) {
     const uint4 wa = draw(B, PURPOSE_THERMO, cell, 1u + 2u * j, t);
     const uint4 wb = draw(B, PURPOSE_THERMO, cell, 2u + 2u * j, t);
-    const double U1 = unit53(wa.x, wa.y), U2 = unit53(wa.z, wa.w), U3 = unit53(wb.x, wb.y);
+    const double U1 = unit53(wa.x, wb.x), U2 = unit53(wa.z, wb.z), U3 = unit53(wa.y, wb.y);
     const double x = sqrt(-2.0 * log(1.0 - U1)) * cos(kTwoPi * U2);
     const double t1 = 1.0 + c * x;
     if (!(t1 > 0.0)) continue;
     const double v = t1 * t1 * t1;
-    if (log(U3) < 0.5 * x * x + d - d * v + d * log(v)) {
+    const double x2 = x * x;
+    if (U3 < 1.0 - 0.0331 * (x2 * x2) || log(U3) < 0.5 * x2 + d - d * v + d * log(v)) {
       ehat = d * v * B.kT;
       return true;
     }

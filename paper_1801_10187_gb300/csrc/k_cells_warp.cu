@@ -71,6 +71,14 @@ struct WarpShared {
   };
 };
 
+// Per-cell bead accumulators of one warp (bead variants only): exact int64
+// momentum and energy sums and the bead count of each of the 32 cells.
+struct BeadShared {
+  unsigned long long X[3][32];
+  unsigned long long E[32];
+  int nb[32];
+};
+
 // Shared memory of one block: the span parameters, then one area per warp;
 // kept under 48 KB so that four blocks (the register limit) fit on an SM with
 // room left for L1.
@@ -100,6 +108,7 @@ struct SpanParams {
 };
 constexpr size_t SPAN_SMEM = (sizeof(SpanParams) + 15) & ~(size_t)15;
 constexpr size_t BLOCK_SMEM = SPAN_SMEM + WARPS * WARP_SMEM;
+constexpr size_t BLOCK_SMEM_BEADS = BLOCK_SMEM + WARPS * sizeof(BeadShared);
 
 // floor(x - s) for 0 <= x < 2^22 and s = S 2^-32 in [-1/2, 1/2), exactly:
 // x = i0 + f with i0 = floor(x) (round-down add of 2^23) and f exact; then
@@ -133,8 +142,10 @@ __device__ __forceinline__ float wrap_fast(float x, float L) {
 
 }  // namespace
 
+// Thermostat and bead variants keep more values live through the per-cell
+// phase; they run three blocks per SM with 80 registers instead of spilling.
 template <bool THERMO, int MODE, bool FORCE, bool BEADS>
-__global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restrict__ boxes,
+__global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp(const BoxDev* __restrict__ boxes,
                                                          const int2* __restrict__ spans,
                                                          int nspans, int* err) {
   using R = RecF;
@@ -143,6 +154,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
   const int lane = threadIdx.x & 31;
   WarpShared& W =
       reinterpret_cast<WarpShared*>(smem_ + SPAN_SMEM)[threadIdx.x >> 5];
+  BeadShared& BS = reinterpret_cast<BeadShared*>(smem_ + BLOCK_SMEM)[threadIdx.x >> 5];
   const SpanParams& H = sp_;
   int box_of_params = -1;  // the span parameters depend on the box only
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
@@ -300,21 +312,39 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
       const bool exact64 = __any_sync(FULL, slow);  // a velocity of 1024 or more
 
       // ---- per cell: u (Sec. 3.5), then the energy about u, axis and xi ----
-      // Solute beads join their cell's collision with mass M (Sec. 3.6); the
-      // beads of these 32 cells form one bead group (32-cell groups).
+      // Solute beads join their cell's collision with mass M (Sec. 3.6).  The
+      // 32 cells of the warp are one bead group; its beads are handled one per
+      // lane (grouped copies of cell and velocity), adding exact int64
+      // momentum to their cell's shared sums.
       int gb0 = 0, gnb = 0, nb = 0;
       long long X[3] = {0, 0, 0};
+      auto for_beads = [&](auto&& f) {  // f(slot in the group order, local cell)
+        for (int j0 = 0; j0 < gnb; j0 += 32) {
+          const int j = gb0 + j0 + lane;
+          if (j0 + lane < gnb) f(j, B.bgc[j] - c0);
+        }
+      };
       if (BEADS) {
         const int g = c0 / B.tc;
         gb0 = (int)B.bstart[g];
         gnb = (int)B.bstart[g + 1] - gb0;
-        for (int j = 0; j < gnb; ++j) {
-          const int b = (int)B.border[gb0 + j];
-          if (B.bcell[b] == cell) {
+        if (gnb > 0) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) X[q] += __double2ll_rn((B.Mb * B.svel[3 * b + q]) * 4294967296.0);
-            ++nb;
-          }
+          for (int q = 0; q < 3; ++q) BS.X[q][lane] = 0ull;
+          BS.E[lane] = 0ull;
+          BS.nb[lane] = 0;
+          __syncwarp();
+          for_beads([&](int j, int lc) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              atomicAdd(&BS.X[q][lc],
+                        (unsigned long long)__double2ll_rn((B.Mb * B.bgv[3 * j + q]) * 4294967296.0));
+            atomicAdd(&BS.nb[lc], 1);
+          });
+          __syncwarp();
+          nb = BS.nb[lane];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) X[q] = (long long)BS.X[q][lane];
         }
       }
       const bool occupied = n > 0 || nb > 0;
@@ -352,6 +382,16 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         W.h[0][lane] = 0;
         W.l[0][lane] = 0;
         __syncwarp();
+        if (BEADS && gnb > 0) {  // bead energies about their cell's u
+          for_beads([&](int j, int lc) {
+            const float4 uo = W.prm[0][lc];
+            const double d0 = B.bgv[3 * j] - (double)uo.x, d1 = B.bgv[3 * j + 1] - (double)uo.y,
+                         d2 = B.bgv[3 * j + 2] - (double)uo.z;
+            atomicAdd(&BS.E[lc], (unsigned long long)__double2ll_rn(
+                                     (B.Mb * (d0 * d0 + d1 * d1 + d2 * d2)) * 4294967296.0));
+          });
+          __syncwarp();
+        }
         bool slow_e = false;
         for (int sbase = 0; sbase < N; sbase += STAGE) {
           const int cnt = min(STAGE, N - sbase);
@@ -392,15 +432,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
           if (has_ovf)
             for (uint32_t j = 0; j < novf; ++j)
               if (ovf_cell[j] == (uint32_t)cell) add_energy(ovf + j);
-          if (BEADS)
-            for (int j = 0; j < gnb; ++j) {
-              const int b = (int)B.border[gb0 + j];
-              if (B.bcell[b] == cell) {
-                const double d0 = B.svel[3 * b] - (double)u[0], d1 = B.svel[3 * b + 1] - (double)u[1],
-                             d2 = B.svel[3 * b + 2] - (double)u[2];
-                Ex += __double2ll_rn((B.Mb * (d0 * d0 + d1 * d1 + d2 * d2)) * 4294967296.0);
-              }
-            }
+          if (BEADS && gnb > 0) Ex = (long long)BS.E[lane];
           // Eq. thermo: E_k about u, E^ ~ Gamma(3(N_c-1)/2, kT), xi = sqrt(E^/E_k)
           float E = H.m * (exact64_e ? i64_to_float(Es)
                                      : split_sum_to_float(W.h[0][lane], W.l[0][lane], Es));
@@ -419,25 +451,21 @@ __global__ void __launch_bounds__(BLOCK, 4) k_cells_warp(const BoxDev* __restric
         axis_of(B, t, (uint32_t)cell, ax);  // Sec. 3.6
         W.prm[0][lane] = make_float4(u[0], u[1], u[2], xi);
         W.prm[1][lane] = make_float4(ax[0], ax[1], ax[2], 0.0f);
-        if (BEADS && nb > 0) {
+      }
+      __syncwarp();
+      if (BEADS && gnb > 0) {  // collide the beads with their cell's parameters
+        for_beads([&](int j, int lc) {
+          const float4 pa = W.prm[0][lc], pb = W.prm[1][lc];
           CellParams<float> prm;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            prm.u[q] = u[q];
-            prm.n[q] = ax[q];
-          }
-          prm.xi = xi;
-          for (int j = 0; j < gnb; ++j) {
-            const int b = (int)B.border[gb0 + j];
-            if (B.bcell[b] == cell) {
-              double w[3] = {B.svel[3 * b], B.svel[3 * b + 1], B.svel[3 * b + 2]};
-              collide_bead<true>(B, prm, w, THERMO);
-              B.svel[3 * b] = w[0];
-              B.svel[3 * b + 1] = w[1];
-              B.svel[3 * b + 2] = w[2];
-            }
-          }
-        }
+          prm.u[0] = pa.x; prm.u[1] = pa.y; prm.u[2] = pa.z; prm.xi = pa.w;
+          prm.n[0] = pb.x; prm.n[1] = pb.y; prm.n[2] = pb.z;
+          double w[3] = {B.bgv[3 * j], B.bgv[3 * j + 1], B.bgv[3 * j + 2]};
+          collide_bead<true>(B, prm, w, THERMO);
+          const uint32_t b = B.border[j];
+          B.svel[3 * b] = w[0];
+          B.svel[3 * b + 1] = w[1];
+          B.svel[3 * b + 2] = w[2];
+        });
       }
       __syncwarp();
     }
@@ -601,9 +629,10 @@ static void* warp_variant(bool thermo, bool force, bool beads, int mode) {
 
 int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, int mode) {
   const void* fn = warp_variant(thermo, force, beads, mode);
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BLOCK_SMEM);
+  const size_t smem = beads ? BLOCK_SMEM_BEADS : BLOCK_SMEM;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, BLOCK_SMEM);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, smem);
   return nb;
 }
 
@@ -612,7 +641,7 @@ void launch_cells_warp(bool thermo, bool force, bool beads, int mode, const BoxD
   if (nspans <= 0) return;
   void* args[] = {(void*)&boxes, (void*)&spans, (void*)&nspans, (void*)&err};
   cudaLaunchKernel(warp_variant(thermo, force, beads, mode), dim3(grid), dim3(BLOCK), args,
-                   BLOCK_SMEM, s);
+                   beads ? BLOCK_SMEM_BEADS : BLOCK_SMEM, s);
 }
 
 }  // namespace mpcd

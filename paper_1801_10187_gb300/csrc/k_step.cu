@@ -232,7 +232,12 @@ __global__ void k_bead_scatter(const BoxDev* __restrict__ boxes, const int2* __r
     const int b1 = min(tt.y + PTILE, B.nbead);
     for (int b = tt.y + threadIdx.x; b < b1; b += blockDim.x) {
       const uint64_t k = B.bkey[b];
-      B.border[B.bstart[(uint32_t)(k >> 32)] + (uint32_t)k] = (uint32_t)b;
+      const uint32_t slot = B.bstart[(uint32_t)(k >> 32)] + (uint32_t)k;
+      B.border[slot] = (uint32_t)b;
+      B.bgc[slot] = B.bcell[b];
+      B.bgv[3 * slot] = B.svel[3 * b];
+      B.bgv[3 * slot + 1] = B.svel[3 * b + 1];
+      B.bgv[3 * slot + 2] = B.svel[3 * b + 2];
     }
   }
 }

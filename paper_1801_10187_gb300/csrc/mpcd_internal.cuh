@@ -92,6 +92,8 @@ struct BoxDev {
   int32_t* bcell;   // bead cell id of the current step
   uint64_t* bkey;   // bead (group << 32 | slot)
   uint32_t* border; // bead indices grouped by bead group
+  int32_t* bgc;     // cell of each grouped bead (same order as border)
+  double* bgv;      // velocity of each grouped bead, 3 per bead
   uint32_t* bcount; // per bead group histogram
   uint32_t* bstart; // nctiles + 1
   // updated on the device
