@@ -77,16 +77,24 @@ class ServeStats:
 
 
 class Server:
+    """``batch_factory`` and ``footprint_fn`` default to the library's batch and
+    footprint calls; the scheduling logic itself runs on the host."""
+
     def __init__(self, precision: str = "mixed", max_bytes: int = 0, max_boxes: int = 512,
-                 max_chunk: int = 200, stream=None, keep_state: bool = False):
+                 max_chunk: int = 200, stream=None, keep_state: bool = False,
+                 batch_factory=None, footprint_fn=None):
         self.precision = precision
         self.max_bytes = int(max_bytes)
         self.max_boxes = int(max_boxes)
         self.max_chunk = int(max_chunk)
         self.keep_state = keep_state
-        self.batch = Batch(precision, stream=stream, max_bytes=self.max_bytes)
+        make = batch_factory or (lambda: Batch(precision, stream=stream, max_bytes=self.max_bytes))
+        self.batch = make()
+        self._footprint = footprint_fn
 
     def footprint(self, job: Job) -> int:
+        if self._footprint is not None:
+            return int(self._footprint(job))
         return box_footprint(job.particles, precision=self.precision, **job.box_kwargs())
 
     def run(self, jobs, realtime: bool = True) -> ServeStats:
