@@ -206,6 +206,24 @@ def sources_hash(paths):
     return h.hexdigest()[:16]
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself without a process
+    group): each rank's elapsed time is reduced to the job's wall time."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank processed units_per_rank (replicas, weak
+    scaling) within the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -292,12 +310,8 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = N * K * world / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    value = job_rate(N * K, world, ms * 1e-3)
 
     # ---- per-phase times (event-timed eager steps, same stream) ----
     phases = box.phase_times(min(K, 50))
