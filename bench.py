@@ -38,6 +38,8 @@ sys.path.insert(0, ROOT)
 from paper_1801_10187_gb300 import inputs  # noqa: E402
 
 FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 (non-tensor) rate
+FP64_FLOPS_PER_PARTICLE = 66     # algorithmic FP64 flops per particle-step
 METRIC = "MPCD particle-steps/s"
 UNIT = "particle-steps/s"
 # kernels launched per step: the fused cell kernel and the record update; the
@@ -330,6 +332,18 @@ def main():
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
                 "alg_bytes_per_particle": step_bytes}
+    if cfg["precision"] == "fp64":
+        # The FP64 model is bound by the FP64 pipe, not by HBM: on GB300 FP64
+        # runs at 1/64 of the FP32 rate.  Algorithmic FP64 flops per particle
+        # and step: collide 36 (difference, Rodrigues rotation, sum), cell sums
+        # 6, stream 12, wrap 6, binning 6 (an FMA counts two).
+        flops = FP64_FLOPS_PER_PARTICLE * s.pos.shape[0] / (dom_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": f"{kname} (collide t + stream/bin t+1)",
+                    "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": flops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                    "alg_flops_per_particle": FP64_FLOPS_PER_PARTICLE,
+                    "hbm_frac": achieved / hbm_peak}
     step_gbs = step_bytes * N * K / (ms * 1e-3) / 1e9 / world
     hbm_step = {"bytes_per_particle_step": step_bytes, "achieved_gbs": step_gbs,
                 "frac_of_peak": step_gbs / hbm_peak, "frac_of_8tbs": step_gbs / 8000.0,
