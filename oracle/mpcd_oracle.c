@@ -191,7 +191,6 @@ int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, 
     float kk = 1.5f * (float)(nc - 1);
     float d = kk - 1.0f / 3.0f;
     float c = 1.0f / sqrtf(9.0f * d);
-    double dd = (double)d, cd = (double)c;
     float kTf = (float)kT;
     for (uint32_t j = 0; j < 64; ++j) {
       /* Attempt j: block A = counter (cell, 1 + 2j).  Its words 0, 2 and 1 are
@@ -216,19 +215,7 @@ int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, 
       }
       float lhs = log_series_f(U3);
       float rhs = 0.5f * x2 + d - d * v + d * log_series_f(v);
-      float diff = lhs - rhs;
-      int accept;
-      if (fabsf(diff) > 1e-3f * (1.0f + d)) {
-        accept = diff < 0.0f;
-      } else {
-        /* Too close to the acceptance boundary for float rounding to decide:
-         * decide in double from the same high words. */
-        double xd = sqrt(-2.0 * log((double)e1)) * cos(TWO_PI * ((double)wa[2] * 0x1p-32));
-        double td = 1.0 + cd * xd;
-        if (!(td > 0.0)) continue;
-        double vd = td * td * td;
-        accept = log((double)U3) < 0.5 * xd * xd + dd - dd * vd + dd * log(vd);
-      }
+      int accept = lhs < rhs;
       if (accept) {
         *ehat = (double)(d * v * kTf);
         return 0;
