@@ -187,20 +187,9 @@ __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, u
 // region, so it accepts without logarithms).  Attempt j reads Philox block
 // A = counter (cell, 1 + 2j): words 0, 2, 1 are the high words of U1, U2, U3;
 // the FP64 sampler takes the low words from block B = (cell, 2 + 2j).  The
-// float version settles acceptances within 1e-3 (1 + d) of the boundary in
-// double from the same words.  Returns false after 64 rejections.
+// float version decides every acceptance in float, with the same series as
+// the oracle's mixed model.  Returns false after 64 rejections.
 // ---------------------------------------------------------------------------
-static __device__ __noinline__ bool gamma_accept_double(float d, float c, uint32_t w0, uint32_t w2,
-                                                 float U3, bool& ok) {
-  const double xd = sqrt(-2.0 * log((double)comp_word_to_float(w0) * 0x1p-32)) *
-                    cos(kTwoPi * ((double)w2 * 0x1p-32));
-  const double td = 1.0 + (double)c * xd;
-  ok = td > 0.0;
-  if (!ok) return false;
-  const double vd = td * td * td, dd = (double)d;
-  return log((double)U3) < 0.5 * xd * xd + dd - dd * vd + dd * log(vd);
-}
-
 __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
                                   float& ehat) {
   const float kk = 1.5f * small_to_float(nc - 1);
@@ -218,18 +207,7 @@ __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_
     const float v = t1 * t1 * t1;
     const float x2 = x * x;
     bool accept = U3 < 1.0f - 0.0331f * (x2 * x2);
-    if (!accept) {
-      const float lhs = series_log(U3);
-      const float rhs = 0.5f * x2 + d - d * v + d * series_log(v);
-      const float diff = lhs - rhs;
-      if (fabsf(diff) > 1e-3f * (1.0f + d)) {
-        accept = diff < 0.0f;
-      } else {
-        bool ok;
-        accept = gamma_accept_double(d, c, wa.x, wa.z, U3, ok);
-        if (!ok) continue;
-      }
-    }
+    if (!accept) accept = series_log(U3) < 0.5f * x2 + d - d * v + d * series_log(v);
     if (accept) {
       ehat = d * v * B.kT_f;
       return true;
