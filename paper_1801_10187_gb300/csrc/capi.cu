@@ -177,7 +177,8 @@ struct Engine {
       for (int v = 0; v < 16; ++v) {
         if (v & 4)
           cells_bps[m][v] =
-              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, m) : 1;
+              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, m)
+                    : cells_warpd_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, m);
         else if (v < 4)
           cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
         else
@@ -310,7 +311,7 @@ struct Engine {
       rec.push_back(b->d);
       const BoxDev& d = b->d;
       int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0);
-      if (mixed && !d.walls && d.K <= WARP_MAX_K &&
+      if (!d.walls && d.K <= WARP_MAX_K &&
           std::max(d.n[0], std::max(d.n[1], d.n[2])) < (1 << 22)) {
         const bool force = d.g[0] != 0.0 || d.g[1] != 0.0 || d.g[2] != 0.0;
         variant = 4 | (d.thermostat ? 1 : 0) | (force ? 2 : 0) | (d.nbead > 0 ? 8 : 0);
@@ -360,9 +361,12 @@ struct Engine {
     for (int v = 0; v < 16; ++v) {
       if (n_spans[v] == 0) continue;
       const int grid = grid_for(n_spans[v], cells_bps[mode][v]);
-      if (v & 4)
+      if ((v & 4) && mixed)
         launch_cells_warp((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, mode, d_boxes, d_spans[v],
                           n_spans[v], grid, d_err, stream);
+      else if (v & 4)
+        launch_cells_warpd((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, mode, d_boxes, d_spans[v],
+                           n_spans[v], grid, d_err, stream);
       else
         launch_cells(mixed, v, mode, d_boxes, d_spans[v], n_spans[v], grid, d_err, stream);
     }

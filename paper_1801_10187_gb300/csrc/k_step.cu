@@ -34,7 +34,9 @@ __device__ __forceinline__ void bond_force(const BoxDev& B, const double* __rest
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       d[k] = sr[3 * o + k] - sr[3 * j + k];
-      d[k] = d[k] - B.L[k] * rint(d[k] / B.L[k]);  // minimum image
+      // minimum image; a bond shorter than L/4 needs no image (rint gives 0),
+      // which saves the FP64 division on nearly every bond
+      if (!(fabs(d[k]) < 0.25 * B.L[k])) d[k] = d[k] - B.L[k] * rint(d[k] / B.L[k]);
     }
     const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     if (!(dist > 0.0)) continue;

@@ -21,6 +21,10 @@ constexpr int WARP_MAX_K = 448;
 int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, int mode);
 void launch_cells_warp(bool thermo, bool force, bool beads, int mode, const BoxDev* boxes,
                        const int2* spans, int nspans, int grid, int* err, cudaStream_t s);
+// The FP64 model's counterpart (k_cells_warp_d.cu), same conditions.
+int cells_warpd_blocks_per_sm(bool thermo, bool force, bool beads, int mode);
+void launch_cells_warpd(bool thermo, bool force, bool beads, int mode, const BoxDev* boxes,
+                        const int2* spans, int nspans, int grid, int* err, cudaStream_t s);
 // Place n particles (device arrays of float (mixed) or double, n x 3) in the
 // current rows of a box whose counts are zero.
 void launch_load(bool mixed, const BoxDev* box, const void* pos, const void* vel, int n, int* err,
