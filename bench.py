@@ -253,7 +253,6 @@ def main():
     config = {"workload": args.workload, "cells": list(cfg["n"]), "density": cfg["density"],
               "precision": cfg["precision"], "thermostat": cfg["thermostat"],
               "alpha_deg": cfg["alpha_deg"], "dt": cfg["dt"], "kT": cfg["kT"],
-              "sort_period": cfg.get("sort_period", 0) or 25,
               "particles_per_gpu": int(round(cfg["density"] * np.prod(cfg["n"]))),
               "parallelism": f"replicas{world}" if world > 1 else "single"}
     if cfg.get("n_chains"):

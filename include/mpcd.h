@@ -9,7 +9,9 @@
  *   [solute velocity-Verlet substeps]           Sec. 2 / Sec. 3.6 (solute)
  *   ballistic streaming r <- r + v dt           Sec. 2, Eq. (stream)
  *   random grid shift, binning into cells       Sec. 2, Sec. 3.4
- *   [periodic reorder of particles by cell]     Sec. 3.8
+ *     (each particle record is appended to the row of its new cell, so the
+ *      particles are grouped by cell every step: the reorder of Sec. 3.8 is
+ *      part of binning)
  *   per-cell mass / momentum / kinetic energy   Sec. 3.5
  *   per-cell random axis [+ MB thermostat]      Sec. 3.6, Eq. (thermo)
  *   v <- u + xi R(alpha) (v - u)                Sec. 2, Eq. (srd); Sec. 3.6 algorithm
@@ -60,8 +62,9 @@ typedef struct {
   double mass;           /* solvent particle mass m [1]                      */
   uint64_t seed;         /* seed of all random draws                         */
   int32_t thermostat;    /* 1: Maxwell-Boltzmann cell thermostat (Eq. thermo)*/
-  int32_t sort_period;   /* reorder particles every k steps (Sec. 3.8) [25]; */
-                         /* 0 = 25, negative = never                         */
+  int32_t sort_period;   /* accepted for the reorder period of Sec. 3.8 [25]; */
+                         /* records are grouped by cell every step here, so  */
+                         /* it does not change the work or the results       */
   int32_t walls_z;       /* 1: no-slip bounce-back walls at z = 0, z = n_z   */
   int32_t reserved0;
   double body_force[3];  /* constant acceleration g; g_z must be 0 w/ walls  */
