@@ -14,11 +14,13 @@
 // are each captured once into a CUDA graph and replayed; step counters and the
 // buffer flips live in the device records.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -105,6 +107,130 @@ int validate(const mpcd_params* p, int precision_expected) {
   const int64_t C = cells_of(*p);
   if (C > 2000000000LL) return fail(MPCD_EINVAL, "too many cells (max 2e9)");
   return MPCD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host <-> device transfer of the solvent state.  The host arrays are double;
+// the mixed model keeps float on the device.  The values move in chunks of
+// XFER_ELEMS: host threads convert (or copy) each chunk into a page-locked
+// slot and queue a cudaMemcpyAsync from it, so conversion, DMA and page
+// faults of fresh host buffers proceed in parallel.  Slots come from a
+// process-wide pool and are kept for reuse by later transfers and contexts.
+// ---------------------------------------------------------------------------
+constexpr size_t XFER_ELEMS = size_t(1) << 19;
+constexpr size_t XFER_SLOT_BYTES = XFER_ELEMS * sizeof(double);
+constexpr int XFER_MAX_THREADS = 16;
+
+std::mutex g_slot_mu;
+std::vector<void*> g_free_slots;
+
+void* take_slot() {
+  {
+    std::lock_guard<std::mutex> lk(g_slot_mu);
+    if (!g_free_slots.empty()) {
+      void* q = g_free_slots.back();
+      g_free_slots.pop_back();
+      return q;
+    }
+  }
+  void* q = nullptr;
+  return cudaMallocHost(&q, XFER_SLOT_BYTES) == cudaSuccess ? q : nullptr;
+}
+
+void give_slot(void* q) {
+  if (!q) return;
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  g_free_slots.push_back(q);
+}
+
+// One host array and its device counterpart (n values each).
+struct XferSeg {
+  double* host;
+  void* dev;
+  size_t n;
+};
+
+// Moves every segment host -> device (to_dev) or device -> host, converting
+// between double and float when mixed.  Returns the first CUDA error.
+cudaError_t transfer(bool to_dev, bool mixed, const XferSeg* seg, int nseg, int device,
+                     cudaStream_t stream) {
+  const size_t es = mixed ? sizeof(float) : sizeof(double);
+  std::vector<size_t> first(nseg + 1, 0);  // first chunk of each segment
+  for (int i = 0; i < nseg; ++i)
+    first[i + 1] = first[i] + (seg[i].n + XFER_ELEMS - 1) / XFER_ELEMS;
+  const size_t nchunks = first[nseg];
+  if (nchunks == 0) return cudaSuccess;
+  std::atomic<size_t> next{0};
+  std::atomic<int> err{(int)cudaSuccess};
+
+  auto work = [&](bool set_device) {
+    if (set_device) cudaSetDevice(device);
+    void* slot[2] = {take_slot(), take_slot()};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = (slot[0] && slot[1]) ? cudaSuccess : cudaErrorMemoryAllocation;
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+      e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+    bool used[2] = {false, false};
+    for (size_t i = 0; e == cudaSuccess && err.load() == (int)cudaSuccess; ++i) {
+      const size_t k = next.fetch_add(1);
+      if (k >= nchunks) break;
+      int s = 0;
+      while (k >= first[s + 1]) ++s;
+      const size_t off = (k - first[s]) * XFER_ELEMS;
+      const size_t len = std::min(XFER_ELEMS, seg[s].n - off);
+      char* dev = (char*)seg[s].dev + off * es;
+      const int j = (int)(i & 1);
+      if (to_dev) {
+        if (used[j] && (e = cudaEventSynchronize(ev[j])) != cudaSuccess) break;
+        const double* src = seg[s].host + off;
+        if (mixed) {
+          float* dst = (float*)slot[j];
+          for (size_t q = 0; q < len; ++q) dst[q] = (float)src[q];
+        } else {
+          std::memcpy(slot[j], src, len * sizeof(double));
+        }
+        if ((e = cudaMemcpyAsync(dev, slot[j], len * es, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+          break;
+      } else {
+        if ((e = cudaMemcpyAsync(slot[j], dev, len * es, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+          break;
+      }
+      if ((e = cudaEventRecord(ev[j], stream)) != cudaSuccess) break;
+      used[j] = true;
+      if (!to_dev) {
+        if ((e = cudaEventSynchronize(ev[j])) != cudaSuccess) break;
+        double* dst = seg[s].host + off;
+        if (mixed) {
+          const float* src = (const float*)slot[j];
+          for (size_t q = 0; q < len; ++q) dst[q] = (double)src[q];
+        } else {
+          std::memcpy(dst, slot[j], len * sizeof(double));
+        }
+      }
+    }
+    // a slot goes back to the pool only once its copy has finished
+    for (int j = 0; j < 2; ++j) {
+      if (ev[j]) {
+        const cudaError_t w = used[j] ? cudaEventSynchronize(ev[j]) : cudaSuccess;
+        if (e == cudaSuccess) e = w;
+        cudaEventDestroy(ev[j]);
+      }
+      give_slot(slot[j]);
+    }
+    if (e != cudaSuccess) {
+      int ok = (int)cudaSuccess;
+      err.compare_exchange_strong(ok, (int)e);
+    }
+  };
+
+  unsigned hw = std::thread::hardware_concurrency();
+  const size_t nthreads =
+      std::min<size_t>(nchunks, std::max<unsigned>(1u, std::min<unsigned>(hw, XFER_MAX_THREADS)));
+  std::vector<std::thread> pool;
+  for (size_t t = 1; t < nthreads; ++t) pool.emplace_back(work, true);
+  work(false);
+  for (auto& th : pool) th.join();
+  return (cudaError_t)err.load();
 }
 
 struct Box {
@@ -628,19 +754,9 @@ struct Engine {
                    const double* svel, uint64_t step) {
     const size_t n3 = (size_t)b->nsol * 3;
     if (b->nsol > 0) {
-      if (mixed) {
-        std::vector<float> hp(n3), hv(n3);
-        for (size_t i = 0; i < n3; ++i) {
-          hp[i] = (float)pos[i];
-          hv[i] = (float)vel[i];
-        }
-        CUDA_TRY(cudaMemcpyAsync(b->stage_r, hp.data(), n3 * 4, cudaMemcpyHostToDevice, stream));
-        CUDA_TRY(cudaMemcpyAsync(b->stage_v, hv.data(), n3 * 4, cudaMemcpyHostToDevice, stream));
-        CUDA_TRY(cudaStreamSynchronize(stream));
-      } else {
-        CUDA_TRY(cudaMemcpyAsync(b->stage_r, pos, n3 * 8, cudaMemcpyHostToDevice, stream));
-        CUDA_TRY(cudaMemcpyAsync(b->stage_v, vel, n3 * 8, cudaMemcpyHostToDevice, stream));
-      }
+      const XferSeg seg[2] = {{const_cast<double*>(pos), b->stage_r, n3},
+                              {const_cast<double*>(vel), b->stage_v, n3}};
+      CUDA_TRY(transfer(true, mixed, seg, 2, device, stream));
     }
     return place(b, b->stage_r, b->stage_v, spos, svel, step);
   }
@@ -674,17 +790,11 @@ struct Engine {
     if (rc) return rc;
     const size_t n3 = (size_t)b->nsol * 3;
     if (b->nsol > 0 && (pos || vel)) {
-      if (mixed) {
-        std::vector<float> hp(pos ? n3 : 0), hv(vel ? n3 : 0);
-        if (pos) CUDA_TRY(cudaMemcpyAsync(hp.data(), b->stage_r, n3 * 4, cudaMemcpyDeviceToHost, stream));
-        if (vel) CUDA_TRY(cudaMemcpyAsync(hv.data(), b->stage_v, n3 * 4, cudaMemcpyDeviceToHost, stream));
-        CUDA_TRY(cudaStreamSynchronize(stream));
-        for (size_t i = 0; pos && i < n3; ++i) pos[i] = (double)hp[i];
-        for (size_t i = 0; vel && i < n3; ++i) vel[i] = (double)hv[i];
-      } else {
-        if (pos) CUDA_TRY(cudaMemcpyAsync(pos, b->stage_r, n3 * 8, cudaMemcpyDeviceToHost, stream));
-        if (vel) CUDA_TRY(cudaMemcpyAsync(vel, b->stage_v, n3 * 8, cudaMemcpyDeviceToHost, stream));
-      }
+      XferSeg seg[2];
+      int nseg = 0;
+      if (pos) seg[nseg++] = {pos, b->stage_r, n3};
+      if (vel) seg[nseg++] = {vel, b->stage_v, n3};
+      CUDA_TRY(transfer(false, mixed, seg, nseg, device, stream));
     }
     if (b->nbead > 0) {
       if (spos) CUDA_TRY(cudaMemcpyAsync(spos, b->d.spos, sizeof(double) * 3 * b->nbead,
