@@ -29,6 +29,10 @@ PURPOSE_SHIFT = 0x53484654
 PURPOSE_ROT = 0x524F5441
 PURPOSE_THERMO = 0x54484D4F
 PURPOSE_VIRT = 0x56495254
+PURPOSE_AT = 0x414E4452
+
+SRD = 0  # collision rules
+AT = 1
 
 
 def build(force: bool = False) -> str:
@@ -55,7 +59,7 @@ class _Params(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("chain_len", ctypes.c_int32),
         ("md_substeps", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
         ("solute_mass", ctypes.c_double),
         ("bond_k", ctypes.c_double),
         ("bond_r0", ctypes.c_double),
@@ -80,6 +84,7 @@ def _load():
         _lib.oracle_axis.argtypes = [u64, u64, ctypes.c_uint32, i32, P(d)]
         _lib.oracle_gamma_draw.argtypes = [u64, u64, ctypes.c_uint32, i32, d, i32, P(d)]
         _lib.oracle_gamma_draw.restype = i32
+        _lib.oracle_at_draw.argtypes = [u64, u64, ctypes.c_uint32, i32, d, i32, P(d)]
         _lib.oracle_step.argtypes = [P(_Params), i64, P(d), P(d), i64, P(d), P(d), P(u64), i64,
                                      P(i32), P(i32)]
         _lib.oracle_step.restype = i32
@@ -111,6 +116,7 @@ class Params:
     solute_mass: float = 1.0
     bond_k: float = 0.0
     bond_r0: float = 0.0
+    collision: int = SRD
 
     def c(self) -> _Params:
         p = _Params()
@@ -130,6 +136,7 @@ class Params:
         p.solute_mass = self.solute_mass
         p.bond_k = self.bond_k
         p.bond_r0 = self.bond_r0
+        p.collision = int(self.collision)
         return p
 
 
@@ -176,6 +183,14 @@ def gamma_draw(seed: int, t: int, cell: int, nc: int, kT: float, precision: int 
     if st != 0:
         raise RuntimeError(f"oracle_gamma_draw status {st}")
     return e.value
+
+
+def at_draw(seed: int, t: int, tag: int, kind: int, sigma: float, precision: int = FP64):
+    """Random velocity of particle ``tag`` (kind 0 solvent, 1 bead) at step t
+    for the Andersen-thermostat rule (Sec. 3.7)."""
+    dv = np.zeros(3)
+    _load().oracle_at_draw(seed, t, tag, kind, sigma, precision, _dptr(dv))
+    return dv
 
 
 def num_cells(params: Params) -> int:

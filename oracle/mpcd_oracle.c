@@ -247,6 +247,42 @@ int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 2, Eq. (at) and Sec. 3.7: the Andersen-thermostat rule draws a       */
+/* Gaussian random velocity for every particle by Box-Muller, keyed by the   */
+/* step, the particle's tag and the seed.  One Box-Muller pair gives         */
+/* components 0 and 1 (cos and sin branches), a second pair's cos branch    */
+/* component 2.                                                             */
+/* ------------------------------------------------------------------------ */
+void oracle_at_draw(uint64_t seed, uint64_t t, uint32_t tag, int32_t kind, double sigma,
+                    int32_t precision, double dv[3]) {
+  uint32_t wa[4];
+  draw4(seed, ORACLE_PURPOSE_AT, tag, 2u * (uint32_t)kind, t, wa);
+  if (precision == ORACLE_MIXED) {
+    /* 1 - U = (2^32 - w) 2^-32 lies in (0, 1], so the logarithm is finite. */
+    float e1 = (float)(4294967296LL - (int64_t)wa[0]) * 0x1p-32f;
+    float e2 = (float)(4294967296LL - (int64_t)wa[2]) * 0x1p-32f;
+    float r1 = sqrtf(-2.0f * log_series_f(e1));
+    float r2 = sqrtf(-2.0f * log_series_f(e2));
+    float c1, s1, c2, s2;
+    cos_sin_turn_f(wa[1], &c1, &s1);
+    cos_sin_turn_f(wa[3], &c2, &s2);
+    float sg = (float)sigma;
+    dv[0] = (double)(sg * (r1 * c1));
+    dv[1] = (double)(sg * (r1 * s1));
+    dv[2] = (double)(sg * (r2 * c2));
+    return;
+  }
+  uint32_t wb[4];
+  draw4(seed, ORACLE_PURPOSE_AT, tag, 2u * (uint32_t)kind + 1u, t, wb);
+  double U1 = u01_53(wa[0], wb[0]), U2 = u01_53(wa[1], wb[1]);
+  double U3 = u01_53(wa[2], wb[2]), U4 = u01_53(wa[3], wb[3]);
+  double r1 = sqrt(-2.0 * log(1.0 - U1)), r2 = sqrt(-2.0 * log(1.0 - U3));
+  dv[0] = sigma * (r1 * cos(TWO_PI * U2));
+  dv[1] = sigma * (r1 * sin(TWO_PI * U2));
+  dv[2] = sigma * (r2 * cos(TWO_PI * U4));
+}
+
+/* ------------------------------------------------------------------------ */
 /* Geometry helpers                                                          */
 /* ------------------------------------------------------------------------ */
 int64_t oracle_num_cells(const oracle_params* p) {
@@ -501,6 +537,10 @@ typedef struct {
   double* u;      /* centre-of-mass velocity (3 per cell) */
   double* axis;   /* rotation axis (3 per cell) */
   double* xi;     /* thermostat scale factor */
+  double* D;      /* FP64, Andersen rule: sum m dv (3 per cell) */
+  int64_t* Qd;    /* MIXED, Andersen rule: solvent sum of rne(dv 2^32) */
+  int64_t* Qdx;   /* MIXED, Andersen rule: beads sum of rne(M dv 2^32) */
+  double* dbar;   /* Andersen rule: mass-weighted mean random velocity (3 per cell) */
 } cellbuf;
 
 static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* vel, int64_t nb,
@@ -605,6 +645,68 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     } else {
       for (int k = 0; k < 3; ++k) cb->u[3 * c + k] = cb->P[3 * c + k] / cb->M[c];
     }
+  }
+
+  /* Andersen-thermostat rule, Eq. (at) and Sec. 3.7: a Gaussian random
+   * velocity dv_i for every member, its mass-weighted mean over the cell,
+   * dbar = sum m_i dv_i / sum m_i (the paper's (1/Nc) sum dv_j when all masses
+   * are equal), and v_i <- u + dv_i - dbar. */
+  if (p->collision == ORACLE_AT) {
+    const double sig = sqrt(p->kT / m), sigb = sqrt(p->kT / Mb);
+    double dv[3];
+    if (mixed) {
+      memset(cb->Qd, 0, sizeof(int64_t) * 3 * ncells);
+      memset(cb->Qdx, 0, sizeof(int64_t) * 3 * ncells);
+    } else {
+      memset(cb->D, 0, sizeof(double) * 3 * ncells);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t c = cellid[i];
+      oracle_at_draw(p->seed, t, (uint32_t)i, 0, sig, p->precision, dv);
+      for (int k = 0; k < 3; ++k) {
+        if (mixed) cb->Qd[3 * c + k] += llrint(dv[k] * 0x1p32);
+        else cb->D[3 * c + k] += m * dv[k];
+      }
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+      int32_t c = cellid[n + b];
+      oracle_at_draw(p->seed, t, (uint32_t)b, 1, sigb, p->precision, dv);
+      for (int k = 0; k < 3; ++k) {
+        if (mixed) cb->Qdx[3 * c + k] += llrint((Mb * dv[k]) * 0x1p32);
+        else cb->D[3 * c + k] += Mb * dv[k];
+      }
+    }
+    for (int64_t c = 0; c < ncells; ++c) {
+      if (cb->cnt[c] == 0) continue;
+      if (mixed) {
+        float Mt = mf * (float)cb->nsol[c] + (float)cb->nbead[c] * Mbf;
+        for (int k = 0; k < 3; ++k) {
+          float Pd = mf * (float)cb->Qd[3 * c + k] + (float)cb->Qdx[3 * c + k];
+          cb->dbar[3 * c + k] = (double)((Pd * 0x1p-32f) / Mt);
+        }
+      } else {
+        for (int k = 0; k < 3; ++k) cb->dbar[3 * c + k] = cb->D[3 * c + k] / cb->M[c];
+      }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t c = cellid[i];
+      oracle_at_draw(p->seed, t, (uint32_t)i, 0, sig, p->precision, dv);
+      for (int k = 0; k < 3; ++k) {
+        if (mixed) {
+          float w = (float)cb->u[3 * c + k] + (float)dv[k];
+          vel[3 * i + k] = (double)(w - (float)cb->dbar[3 * c + k]);
+        } else {
+          vel[3 * i + k] = (cb->u[3 * c + k] + dv[k]) - cb->dbar[3 * c + k];
+        }
+      }
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+      int32_t c = cellid[n + b];
+      oracle_at_draw(p->seed, t, (uint32_t)b, 1, sigb, p->precision, dv);
+      for (int k = 0; k < 3; ++k)
+        svel[3 * b + k] = (cb->u[3 * c + k] + dv[k]) - cb->dbar[3 * c + k];
+    }
+    return status;
   }
 
   /* Thermostat: kinetic energy about u, Eq. (thermo). */
@@ -715,6 +817,8 @@ static int32_t check_params(const oracle_params* p, int64_t n, int64_t nb) {
   if (n < 0 || nb < 0) return -1;
   if (!(p->dt > 0.0) || !(p->mass > 0.0) || !(p->kT >= 0.0)) return -1;
   if (p->walls_z && (p->g[2] != 0.0 || nb > 0)) return -1;
+  if (p->collision != ORACLE_SRD && p->collision != ORACLE_AT) return -1;
+  if (p->collision == ORACLE_AT && (p->thermostat || p->walls_z)) return -1;
   if (nb > 0 && (p->chain_len < 1 || nb % p->chain_len != 0 || p->md_substeps < 1 ||
                  !(p->solute_mass > 0.0)))
     return -1;
@@ -743,6 +847,10 @@ int32_t oracle_step(const oracle_params* p, int64_t n, double* pos, double* vel,
   cb.u = (double*)calloc((size_t)ncells * 3, sizeof(double));
   cb.axis = (double*)calloc((size_t)ncells * 3, sizeof(double));
   cb.xi = (double*)calloc((size_t)ncells, sizeof(double));
+  cb.D = (double*)calloc((size_t)ncells * 3, sizeof(double));
+  cb.Qd = (int64_t*)calloc((size_t)ncells * 3, sizeof(int64_t));
+  cb.Qdx = (int64_t*)calloc((size_t)ncells * 3, sizeof(int64_t));
+  cb.dbar = (double*)calloc((size_t)ncells * 3, sizeof(double));
   int32_t* cellid = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n + nb + 1));
   for (int64_t it = 0; it < nsteps && st == 0; ++it) {
     st = one_step(p, n, pos, vel, nb, spos, svel, *step, cellid, &cb, ncells);
@@ -755,6 +863,7 @@ int32_t oracle_step(const oracle_params* p, int64_t n, double* pos, double* vel,
   free(cb.M); free(cb.P); free(cb.E);
   free(cb.Qs); free(cb.Qx); free(cb.Es); free(cb.Ex);
   free(cb.u); free(cb.axis); free(cb.xi);
+  free(cb.D); free(cb.Qd); free(cb.Qdx); free(cb.dbar);
   return st;
 }
 

@@ -13,6 +13,8 @@
  *   Sec. 3.5             : per-cell mass, momentum and kinetic energy
  *   Sec. 2, Eq. (srd)    : v <- u + R(alpha) (v - u), random axis per cell
  *   Sec. 2, Eq. (thermo) : Maxwell-Boltzmann cell thermostat, xi = sqrt(E^/Ek)
+ *   Sec. 2, Eq. (at)     : Andersen-thermostat collision rule (Sec. 3.7):
+ *                          v <- u + dv_i - <dv>, dv_i Gaussian per particle
  *   Sec. 3.6             : cylindrical-projection axis, Marsaglia-Tsang Gamma
  *                          draw with a Box-Muller normal, xi = 1 if Nc < 2
  *   Sec. 2 / Sec. 3.6    : solute beads (velocity Verlet, harmonic bonds)
@@ -45,6 +47,10 @@ enum { ORACLE_FP64 = 0, ORACLE_MIXED = 1 };
 #define ORACLE_PURPOSE_ROT    0x524F5441u
 #define ORACLE_PURPOSE_THERMO 0x54484D4Fu
 #define ORACLE_PURPOSE_VIRT   0x56495254u
+#define ORACLE_PURPOSE_AT     0x414E4452u
+
+/* Collision rules. */
+enum { ORACLE_SRD = 0, ORACLE_AT = 1 };
 
 typedef struct {
   int32_t n[3];          /* cells per axis; cell edge a = 1, box L_k = n_k   */
@@ -60,7 +66,7 @@ typedef struct {
   int32_t precision;     /* ORACLE_FP64 or ORACLE_MIXED                     */
   int32_t chain_len;     /* beads per chain (solute)                        */
   int32_t md_substeps;   /* velocity-Verlet substeps per collision          */
-  int32_t pad_;
+  int32_t collision;     /* ORACLE_SRD (Eq. srd) or ORACLE_AT (Eq. at)      */
   double solute_mass;    /* bead mass M                                     */
   double bond_k;         /* harmonic bond constant                          */
   double bond_r0;        /* harmonic bond rest length                       */
@@ -89,12 +95,23 @@ void oracle_axis(uint64_t seed, uint64_t t, uint32_t cell, int32_t precision, do
 int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc,
                           double kT, int32_t precision, double* ehat);
 
+/* Random velocity dv of one particle for the Andersen-thermostat rule
+ * (Sec. 3.7): three Gaussian components of standard deviation sigma
+ * (sqrt(kT/m) of that particle) by Box-Muller.  tag: input index of the
+ * particle; kind: 0 solvent, 1 solute bead.  MIXED: one Philox block at
+ * counter (tag, 2 kind) gives (w0, w1) -> components 0, 1 (cos and sin) and
+ * (w2, w3) -> component 2 (cos), all in float; FP64: 53-bit uniforms whose
+ * high words come from that block and low words from (tag, 2 kind + 1). */
+void oracle_at_draw(uint64_t seed, uint64_t t, uint32_t tag, int32_t kind, double sigma,
+                    int32_t precision, double dv[3]);
+
 /* Advance nsteps SRD steps in place.  pos/vel: n*3 (x,y,z per particle);
  * spos/svel: nb*3 bead state (nb a multiple of chain_len).  *step is the
  * step counter t, incremented per step.  If cell_out != NULL it receives the
  * cell id of every particle (solvent then beads) at the last step; if
  * count_out != NULL it receives the member count (solvent + beads) of every
  * cell at the last step (oracle_num_cells entries).
+ * The Andersen rule takes no thermostat flag and no walls (-1 otherwise).
  * Returns 0, -1 invalid argument, -4 Gamma sampler cap reached. */
 int32_t oracle_step(const oracle_params* p, int64_t n, double* pos, double* vel,
                     int64_t nb, double* spos, double* svel, uint64_t* step,
