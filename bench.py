@@ -66,7 +66,7 @@ def workload_cfg(name):
 def box_kwargs(cfg):
     kw = dict(n=cfg["n"], dt=cfg["dt"], alpha_deg=cfg["alpha_deg"], kT=cfg["kT"],
               seed=cfg["seed"], thermostat=cfg["thermostat"], precision=cfg["precision"],
-              sort_period=cfg.get("sort_period", 0))
+              sort_period=cfg.get("sort_period", 0), collision=cfg.get("collision", "srd"))
     if cfg.get("n_chains"):
         kw.update(chain_len=cfg["chain_len"], md_substeps=cfg["md_substeps"],
                   solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"])
@@ -160,7 +160,8 @@ def oracle_rate(cfg, budget_s, steps=None, warmup=0):
     s, sp, sv = make_state(cfg, n=n)
     prec = oracle.MIXED if cfg["precision"] == "mixed" else oracle.FP64
     okw = dict(n=n, dt=cfg["dt"], alpha_deg=cfg["alpha_deg"], kT=cfg["kT"], seed=cfg["seed"],
-               thermostat=cfg["thermostat"], precision=prec)
+               thermostat=cfg["thermostat"], precision=prec,
+               collision=oracle.AT if cfg.get("collision") == "at" else oracle.SRD)
     if cfg.get("n_chains"):
         nch = max(1, int(round(cfg["n_chains"] * np.prod(n) / full_cells)))
         sp, sv = inputs.chains(n, nch, cfg["chain_len"], cfg["bond_r0"], kT=cfg["kT"],

@@ -15,6 +15,10 @@
  *   per-cell mass / momentum / kinetic energy   Sec. 3.5
  *   per-cell random axis [+ MB thermostat]      Sec. 3.6, Eq. (thermo)
  *   v <- u + xi R(alpha) (v - u)                Sec. 2, Eq. (srd); Sec. 3.6 algorithm
+ * or, with the Andersen-thermostat collision rule (collision = MPCD_AT):
+ *   v <- u + dv - <dv>_m, dv Gaussian per       Sec. 2, Eq. (at); Sec. 3.7
+ *   particle, <dv>_m the cell's mass-weighted
+ *   mean of dv
  *
  * Conventions
  *   - Lengths are in units of the cell edge a: the cell edge is 1 and the box
@@ -49,6 +53,17 @@ extern "C" {
 
 typedef enum { MPCD_FP64 = 0, MPCD_MIXED = 1 } mpcd_precision;
 
+/* Collision rules: stochastic rotation (Eq. srd, Sec. 3.6) or the Andersen
+ * thermostat (Eq. at, Sec. 3.7).  The Andersen rule draws, for every member
+ * of a cell, a velocity dv with Gaussian components of variance kT/m_i
+ * (Box-Muller on Philox keyed by seed, step and the particle's tag) and sets
+ * v_i <- u + dv_i - sum_j m_j dv_j / sum_j m_j, which is the paper's
+ * (1/N_c) sum_j dv_j when all masses are equal; solute beads take part with
+ * their mass.  It thermostats by itself, so it takes neither the thermostat
+ * flag nor walls, and it needs a row capacity of at most 448 records
+ * (a density below about 300 per cell). */
+typedef enum { MPCD_SRD = 0, MPCD_AT = 1 } mpcd_collision;
+
 /* SRD parameters (Sec. 2; Sec. 4 benchmark values in brackets).  Plain
  * values, copied at create time. */
 typedef struct {
@@ -66,7 +81,7 @@ typedef struct {
                          /* records are grouped by cell every step here, so  */
                          /* it does not change the work or the results       */
   int32_t walls_z;       /* 1: no-slip bounce-back walls at z = 0, z = n_z   */
-  int32_t reserved0;
+  int32_t collision;     /* mpcd_collision [MPCD_SRD]; alpha is unused by AT */
   double body_force[3];  /* constant acceleration g; g_z must be 0 w/ walls  */
   double virt_density;   /* density of virtual wall particles; 0 = N / V     */
   int32_t chain_len;     /* solute: beads per linear chain (0 = no solute)   */

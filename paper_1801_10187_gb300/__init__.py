@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libmpcd.so")
 
 MPCD_OK, MPCD_EINVAL, MPCD_ENOMEM, MPCD_ECUDA, MPCD_EDEVICE, MPCD_ESTATE = 0, -1, -2, -3, -4, -5
 FP64, MIXED = 0, 1
+SRD, AT = 0, 1  # collision rules (Eq. srd, Eq. at)
 
 
 class MpcdError(RuntimeError):
@@ -44,7 +45,7 @@ class _Params(ctypes.Structure):
         ("thermostat", ctypes.c_int32),
         ("sort_period", ctypes.c_int32),
         ("walls_z", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
         ("body_force", ctypes.c_double * 3),
         ("virt_density", ctypes.c_double),
         ("chain_len", ctypes.c_int32),
@@ -142,7 +143,8 @@ def _as3(a):
 def make_params(n=(10, 10, 10), dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=1,
                 thermostat=False, sort_period=0, walls_z=False, body_force=(0.0, 0.0, 0.0),
                 virt_density=0.0, precision="mixed", chain_len=0, md_substeps=0,
-                solute_mass=1.0, bond_k=0.0, bond_r0=0.0, alpha=None) -> _Params:
+                solute_mass=1.0, bond_k=0.0, bond_r0=0.0, alpha=None,
+                collision="srd") -> _Params:
     p = _Params()
     p.n[:] = [int(x) for x in n]
     p.precision = MIXED if precision in ("mixed", MIXED) else FP64
@@ -162,6 +164,7 @@ def make_params(n=(10, 10, 10), dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=
     p.solute_mass = float(solute_mass)
     p.bond_k = float(bond_k)
     p.bond_r0 = float(bond_r0)
+    p.collision = AT if collision in ("at", AT) else SRD
     return p
 
 

@@ -101,6 +101,10 @@ int validate(const mpcd_params* p, int precision_expected) {
   if (p->walls_z && p->body_force[2] != 0.0)
     return fail(MPCD_EINVAL, "body_force[2] must be 0 with walls_z");
   if (p->walls_z && p->chain_len > 0) return fail(MPCD_EINVAL, "solute with walls is not supported");
+  if (p->collision != MPCD_SRD && p->collision != MPCD_AT)
+    return fail(MPCD_EINVAL, "collision must be MPCD_SRD or MPCD_AT");
+  if (p->collision == MPCD_AT && (p->thermostat || p->walls_z))
+    return fail(MPCD_EINVAL, "the Andersen rule thermostats by itself: no thermostat flag, no walls");
   if (p->chain_len < 0 || p->chain_len > 1024) return fail(MPCD_EINVAL, "chain_len in [0, 1024]");
   if (p->chain_len > 0 && (p->md_substeps < 1 || !(p->solute_mass > 0.0)))
     return fail(MPCD_EINVAL, "solute needs md_substeps >= 1 and solute_mass > 0");
@@ -264,9 +268,11 @@ struct Engine {
   BoxDev* d_boxes = nullptr;
   int n_records = 0;
   // per kernel variant: thermostat (1) | walls or beads (2) | warp-spread members (4);
-  // for the warp-spread kernel bit 2 means a nonzero body force and bit 8 beads
-  int2* d_spans[16] = {};
-  int n_spans[16] = {};
+  // for the warp-spread kernel bit 2 means a nonzero body force, bit 8 beads
+  // and bit 16 the Andersen rule
+  static constexpr int NVAR = 32;
+  int2* d_spans[NVAR] = {};
+  int n_spans[NVAR] = {};
   ScanSeg* d_bsegs = nullptr;
   int2* d_bstiles = nullptr;
   int n_bstiles = 0;
@@ -281,7 +287,7 @@ struct Engine {
   int* d_err = nullptr;
   double* d_partials = nullptr;
   bool any_beads = false;
-  int cells_bps[3][16] = {};
+  int cells_bps[3][NVAR] = {};
 
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // MODE_P, MODE_F, MODE_C
   bool tables_ok = false;
@@ -300,11 +306,12 @@ struct Engine {
       own_stream = true;
     }
     for (int m = 0; m < 3; ++m)
-      for (int v = 0; v < 16; ++v) {
-        if (v & 4)
+      for (int v = 0; v < NVAR; ++v) {
+        const bool at = (v & 16) != 0;
+        if ((v & 4) && !(at && (v & 1)))
           cells_bps[m][v] =
-              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, m)
-                    : cells_warpd_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, m);
+              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, m)
+                    : cells_warpd_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, m);
         else if (v < 4)
           cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
         else
@@ -327,7 +334,7 @@ struct Engine {
     void* ptrs[] = {d_boxes, d_bsegs, d_bstiles, d_btiles, d_mdtiles, d_tsum, d_gscan, d_toff};
     for (void* q : ptrs)
       if (q) cudaFree(q);
-    for (int v = 0; v < 16; ++v) {
+    for (int v = 0; v < NVAR; ++v) {
       if (d_spans[v]) cudaFree(d_spans[v]);
       d_spans[v] = nullptr;
       n_spans[v] = 0;
@@ -423,7 +430,7 @@ struct Engine {
     tables_ok = true;
     if (live.empty()) return MPCD_OK;
     std::vector<BoxDev> rec;
-    std::vector<int2> sp[16], bst, bt, mt;
+    std::vector<int2> sp[NVAR], bst, bt, mt;
     std::vector<ScanSeg> bseg;
     any_beads = false;
     int max_cl = 1;
@@ -440,7 +447,8 @@ struct Engine {
       if (!d.walls && d.K <= WARP_MAX_K &&
           std::max(d.n[0], std::max(d.n[1], d.n[2])) < (1 << 22)) {
         const bool force = d.g[0] != 0.0 || d.g[1] != 0.0 || d.g[2] != 0.0;
-        variant = 4 | (d.thermostat ? 1 : 0) | (force ? 2 : 0) | (d.nbead > 0 ? 8 : 0);
+        variant = 4 | (d.thermostat ? 1 : 0) | (force ? 2 : 0) | (d.nbead > 0 ? 8 : 0) |
+                  (d.collision == RULE_AT ? 16 : 0);
       }
       for (int c0 = 0; c0 < d.ncells; c0 += BLOCK) sp[variant].push_back(make_int2((int)i, c0));
       if (d.nbead > 0) {
@@ -463,7 +471,7 @@ struct Engine {
       return MPCD_OK;
     };
     if ((rc = up(rec, d_boxes, &n_records))) return rc;
-    for (int v = 0; v < 16; ++v)
+    for (int v = 0; v < NVAR; ++v)
       if ((rc = up(sp[v], d_spans[v], &n_spans[v]))) return rc;
     if ((rc = up(bseg, d_bsegs, nullptr))) return rc;
     if ((rc = up(bst, d_bstiles, &n_bstiles))) return rc;
@@ -484,15 +492,16 @@ struct Engine {
   }
 
   void launch_cells_all(int mode) {
-    for (int v = 0; v < 16; ++v) {
+    for (int v = 0; v < NVAR; ++v) {
       if (n_spans[v] == 0) continue;
       const int grid = grid_for(n_spans[v], cells_bps[mode][v]);
+      const bool at = (v & 16) != 0;
       if ((v & 4) && mixed)
-        launch_cells_warp((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, mode, d_boxes, d_spans[v],
-                          n_spans[v], grid, d_err, stream);
+        launch_cells_warp((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, mode, d_boxes,
+                          d_spans[v], n_spans[v], grid, d_err, stream);
       else if (v & 4)
-        launch_cells_warpd((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, mode, d_boxes, d_spans[v],
-                           n_spans[v], grid, d_err, stream);
+        launch_cells_warpd((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, mode, d_boxes,
+                           d_spans[v], n_spans[v], grid, d_err, stream);
       else
         launch_cells(mixed, v, mode, d_boxes, d_spans[v], n_spans[v], grid, d_err, stream);
     }
@@ -653,7 +662,12 @@ struct Engine {
     d.chain_len = p.chain_len;
     d.md_substeps = p.md_substeps;
     d.thermostat = p.thermostat ? 1 : 0;
+    d.collision = p.collision;
     d.K = row_capacity(p, nsol);
+    if (d.collision == RULE_AT &&
+        (d.K > WARP_MAX_K || std::max(p.n[0], std::max(p.n[1], p.n[2])) >= (1 << 22)))
+      return fail(MPCD_EINVAL, "the Andersen rule needs a row capacity <= 448 (density below "
+                               "about 300) and fewer than 2^22 cells per axis");
     d.ovf_cap = (int32_t)std::max<int64_t>(nsol, 1);
     d.tc = BEAD_TILE;
     d.nctiles = (int32_t)((C + BEAD_TILE - 1) / BEAD_TILE);
@@ -668,6 +682,10 @@ struct Engine {
     const double V = (double)p.n[0] * p.n[1] * p.n[2];
     d.virt_density = p.virt_density > 0.0 ? p.virt_density : (double)nsol / V;
     d.sigma_virt = std::sqrt(p.kT / p.mass);
+    d.sig = std::sqrt(p.kT / p.mass);
+    d.sigb = p.solute_mass > 0.0 ? std::sqrt(p.kT / p.solute_mass) : 0.0;
+    d.sig_f = (float)d.sig;
+    d.sigb_f = (float)d.sigb;
     d.ca = std::cos(p.alpha);
     d.sa = std::sin(p.alpha);
     d.omc = 1.0 - d.ca;

@@ -239,6 +239,42 @@ __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_
 }
 
 // ---------------------------------------------------------------------------
+// Eq. (at) / Sec. 3.7: Gaussian random velocity of one particle for the
+// Andersen-thermostat rule, keyed by (seed, step, tag, kind); kind 0 is the
+// solvent, 1 the solute beads.  Box-Muller on Philox block A = counter
+// (tag, 2 kind): words (0, 1) give components 0 and 1 (cos and sin
+// branches), words (2, 3) component 2 (cos).  The float version stays in
+// float with the mixed model's series; the FP64 version takes the low words
+// of its 53-bit uniforms from block B = (tag, 2 kind + 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void at_draw(const BoxDev& B, unsigned long long t, uint32_t tag,
+                                        uint32_t kind, float sigma, float dv[3]) {
+  const uint4 w = draw(B, PURPOSE_AT, tag, 2u * kind, t);
+  const float e1 = comp_word_to_float(w.x) * 0x1p-32f;  // 1 - U in (0, 1]
+  const float e2 = comp_word_to_float(w.z) * 0x1p-32f;
+  const float r1 = sqrtf(-2.0f * series_log(e1));
+  const float r2 = sqrtf(-2.0f * series_log(e2));
+  float c1, s1, c2, s2;
+  turn_cos_sin(w.y, c1, s1);
+  turn_cos_sin(w.w, c2, s2);
+  dv[0] = sigma * (r1 * c1);
+  dv[1] = sigma * (r1 * s1);
+  dv[2] = sigma * (r2 * c2);
+}
+
+__device__ __forceinline__ void at_draw(const BoxDev& B, unsigned long long t, uint32_t tag,
+                                        uint32_t kind, double sigma, double dv[3]) {
+  const uint4 wa = draw(B, PURPOSE_AT, tag, 2u * kind, t);
+  const uint4 wb = draw(B, PURPOSE_AT, tag, 2u * kind + 1u, t);
+  const double U1 = unit53(wa.x, wb.x), U2 = unit53(wa.y, wb.y);
+  const double U3 = unit53(wa.z, wb.z), U4 = unit53(wa.w, wb.w);
+  const double r1 = sqrt(-2.0 * log(1.0 - U1)), r2 = sqrt(-2.0 * log(1.0 - U3));
+  dv[0] = sigma * (r1 * cos(kTwoPi * U2));
+  dv[1] = sigma * (r1 * sin(kTwoPi * U2));
+  dv[2] = sigma * (r2 * cos(kTwoPi * U4));
+}
+
+// ---------------------------------------------------------------------------
 // Walls: virtual particles in the part of a wall-cut cell outside the channel
 // (count with mean rho_v * f_out, Gaussian velocities of variance kT/m).
 // ---------------------------------------------------------------------------

@@ -30,6 +30,11 @@
 // of their cell, as in k_cells.  The int32 parts stay in range while K <= 448
 // and |v| < 1024; a warp that meets a larger velocity (or energy) sums its
 // cells again in int64, one lane per cell.
+//
+// The Andersen-thermostat variant (Eq. at, Sec. 3.7) has the same passes:
+// pass 1 also sums each member's Gaussian random velocity dv (drawn from its
+// tag) in the same exact split form, the cell phase forms the mass-weighted
+// mean dv of the cell, and pass 2 draws dv again and sets v = (u + dv) - dbar.
 #include "dev_collide.cuh"
 #include "dev_rows.cuh"
 #include "dev_stream.cuh"
@@ -79,6 +84,16 @@ struct BeadShared {
   int nb[32];
 };
 
+// Andersen-rule accumulators of one warp: split sums of the random
+// velocities per cell, the tags of the staged members, and the beads' exact
+// int64 random momenta.
+struct ATShared {
+  int h[3][32];
+  int l[3][32];
+  uint32_t tag[STAGE_PAD];
+  unsigned long long DX[3][32];
+};
+
 // Shared memory of one block: the span parameters, then one area per warp;
 // kept under 48 KB so that four blocks (the register limit) fit on an SM with
 // room left for L1.
@@ -109,6 +124,10 @@ struct SpanParams {
 constexpr size_t SPAN_SMEM = (sizeof(SpanParams) + 15) & ~(size_t)15;
 constexpr size_t BLOCK_SMEM = SPAN_SMEM + WARPS * WARP_SMEM;
 constexpr size_t BLOCK_SMEM_BEADS = BLOCK_SMEM + WARPS * sizeof(BeadShared);
+
+__host__ __device__ constexpr size_t block_smem(bool beads, bool at) {
+  return BLOCK_SMEM + (beads ? WARPS * sizeof(BeadShared) : 0) + (at ? WARPS * sizeof(ATShared) : 0);
+}
 
 // floor(x - s) for 0 <= x < 2^22 and s = S 2^-32 in [-1/2, 1/2), exactly:
 // x = i0 + f with i0 = floor(x) (round-down add of 2^23) and f exact; then
@@ -142,10 +161,11 @@ __device__ __forceinline__ float wrap_fast(float x, float L) {
 
 }  // namespace
 
-// Thermostat and bead variants keep more values live through the per-cell
-// phase; they run three blocks per SM with 80 registers instead of spilling.
-template <bool THERMO, int MODE, bool FORCE, bool BEADS>
-__global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp(const BoxDev* __restrict__ boxes,
+// Thermostat, bead and Andersen variants keep more values live through the
+// per-cell phase; they run three blocks per SM with 80 registers instead of
+// spilling.  AT selects the Andersen rule (then THERMO is false).
+template <bool THERMO, int MODE, bool FORCE, bool BEADS, bool AT>
+__global__ void __launch_bounds__(BLOCK, (THERMO || BEADS || AT) ? 3 : 4) k_cells_warp(const BoxDev* __restrict__ boxes,
                                                          const int2* __restrict__ spans,
                                                          int nspans, int* err) {
   using R = RecF;
@@ -155,6 +175,7 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
   WarpShared& W =
       reinterpret_cast<WarpShared*>(smem_ + SPAN_SMEM)[threadIdx.x >> 5];
   BeadShared& BS = reinterpret_cast<BeadShared*>(smem_ + BLOCK_SMEM)[threadIdx.x >> 5];
+  ATShared& AS = reinterpret_cast<ATShared*>(smem_ + block_smem(BEADS, false))[threadIdx.x >> 5];
   const SpanParams& H = sp_;
   int box_of_params = -1;  // the span parameters depend on the box only
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
@@ -248,6 +269,7 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
             W.sv[0][js] = a[u].x;
             W.sv[1][js] = a[u].y;
             W.sv[2][js] = a[u].z;
+            if (AT) AS.tag[js] = __float_as_uint(a[u].w);
           }
         }
       }
@@ -278,13 +300,18 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
       for (int q = 0; q < 3; ++q) {
         W.h[q][lane] = 0;
         W.l[q][lane] = 0;
+        if (AT) {
+          AS.h[q][lane] = 0;
+          AS.l[q][lane] = 0;
+        }
       }
       __syncwarp();
-      bool slow = false;
+      bool slow = false, slow_d = false;
       for (int sbase = 0; sbase < N; sbase += STAGE) {
         const int cnt = min(STAGE, N - sbase);
         stage(sbase, cnt);
         int Hs[3] = {0, 0, 0}, Ls[3] = {0, 0, 0};
+        int Hd[3] = {0, 0, 0}, Ld[3] = {0, 0, 0};
         share(sbase, cnt, [&](int o, int js, bool last) {
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
@@ -297,6 +324,21 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
             Hs[q] += h;
             Ls[q] += l;
           }
+          if (AT) {  // Eq. at: this member's random velocity, summed the same way
+            float dv[3];
+            at_draw(B, t, AS.tag[js], 0u, B.sig_f, dv);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              int h, l;
+              if (!split32(dv[q], h, l)) {
+                slow_d = true;
+                h = 0;
+                l = 0;
+              }
+              Hd[q] += h;
+              Ld[q] += l;
+            }
+          }
           if (last) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -304,12 +346,19 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
               atomicAdd(&W.l[q][o], Ls[q]);
               Hs[q] = 0;
               Ls[q] = 0;
+              if (AT) {
+                atomicAdd(&AS.h[q][o], Hd[q]);
+                atomicAdd(&AS.l[q][o], Ld[q]);
+                Hd[q] = 0;
+                Ld[q] = 0;
+              }
             }
           }
         });
         __syncwarp();
       }
       const bool exact64 = __any_sync(FULL, slow);  // a velocity of 1024 or more
+      const bool exact64_d = AT && __any_sync(FULL, slow_d);
 
       // ---- per cell: u (Sec. 3.5), then the energy about u, axis and xi ----
       // Solute beads join their cell's collision with mass M (Sec. 3.6).  The
@@ -376,6 +425,66 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
           u[q] = (P * 0x1p-32f) / M;
         }
         W.prm[0][lane] = make_float4(u[0], u[1], u[2], 1.0f);
+      }
+      if (AT) {
+        // Eq. at: dbar = sum m dv / sum m over the cell's members and beads
+        long long DX[3] = {0, 0, 0};
+        if (BEADS && gnb > 0) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) AS.DX[q][lane] = 0ull;
+          __syncwarp();
+          for_beads([&](int j, int lc) {
+            float dvf[3];
+            at_draw(B, t, B.border[j], 1u, B.sigb_f, dvf);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              atomicAdd(&AS.DX[q][lc],
+                        (unsigned long long)__double2ll_rn((B.Mb * (double)dvf[q]) * 4294967296.0));
+          });
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 3; ++q) DX[q] = (long long)AS.DX[q][lane];
+        }
+        if (occupied) {
+          long long Qd[3] = {0, 0, 0};
+          auto add_dv = [&](const R* p) {
+            const float4 a = *reinterpret_cast<const float4*>(p);  // (v, tag)
+            float dv[3];
+            at_draw(B, t, __float_as_uint(a.w), 0u, B.sig_f, dv);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) Qd[q] += fix32_rne(dv[q]);
+          };
+          if (exact64_d)
+            for (int k = 0; k < nrow; ++k) add_dv(rows + (size_t)lane * K + k);
+          if (has_ovf)
+            for (uint32_t j = 0; j < novf; ++j)
+              if (ovf_cell[j] == (uint32_t)cell) add_dv(ovf + j);
+          float M = H.m * small_to_float((int)n);
+          if (BEADS) M = M + (small_to_float(nb) * B.Mb_f + 0.0f * H.m);
+          float dbar[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            float D = H.m * (exact64_d ? i64_to_float(Qd[q])
+                                       : split_sum_to_float(AS.h[q][lane], AS.l[q][lane], Qd[q]));
+            if (BEADS) D = D + i64_to_float(DX[q]);
+            dbar[q] = (D * 0x1p-32f) / M;
+          }
+          W.prm[0][lane] = make_float4(u[0], u[1], u[2], 0.0f);
+          W.prm[1][lane] = make_float4(dbar[0], dbar[1], dbar[2], 0.0f);
+        }
+        __syncwarp();
+        if (BEADS && gnb > 0) {  // Eq. at for the beads: v = (u + dv) - dbar
+          for_beads([&](int j, int lc) {
+            const float4 pa = W.prm[0][lc], pb = W.prm[1][lc];
+            const uint32_t b = B.border[j];
+            float dvf[3];
+            at_draw(B, t, b, 1u, B.sigb_f, dvf);
+            B.svel[3 * b] = ((double)pa.x + (double)dvf[0]) - (double)pb.x;
+            B.svel[3 * b + 1] = ((double)pa.y + (double)dvf[1]) - (double)pb.y;
+            B.svel[3 * b + 2] = ((double)pa.z + (double)dvf[2]) - (double)pb.z;
+          });
+        }
+        __syncwarp();
       }
       float xi = 1.0f;
       if (THERMO) {
@@ -446,14 +555,14 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
           }
         }
       }
-      if (occupied) {
+      if (occupied && !AT) {
         float ax[3];
         axis_of(B, t, (uint32_t)cell, ax);  // Sec. 3.6
         W.prm[0][lane] = make_float4(u[0], u[1], u[2], xi);
         W.prm[1][lane] = make_float4(ax[0], ax[1], ax[2], 0.0f);
       }
       __syncwarp();
-      if (BEADS && gnb > 0) {  // collide the beads with their cell's parameters
+      if (BEADS && !AT && gnb > 0) {  // collide the beads with their cell's parameters
         for_beads([&](int j, int lc) {
           const float4 pa = W.prm[0][lc], pb = W.prm[1][lc];
           CellParams<float> prm;
@@ -472,8 +581,15 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
 
     // ---- pass 2: collide (Eq. srd), stream (Eq. stream), bin (Sec. 3.4) ----
     // new state of a member and its cell for the next step
-    auto advance = [&](float r[3], float w[3], int o) -> uint32_t {
-      if (MODE != MODE_P) {
+    auto advance = [&](float r[3], float w[3], uint32_t tag, int o) -> uint32_t {
+      if (MODE != MODE_P && AT) {  // Eq. at
+        const float4 pa = W.prm[0][o], pb = W.prm[1][o];
+        float dv[3];
+        at_draw(B, t, tag, 0u, B.sig_f, dv);
+        w[0] = (pa.x + dv[0]) - pb.x;
+        w[1] = (pa.y + dv[1]) - pb.y;
+        w[2] = (pa.z + dv[2]) - pb.z;
+      } else if (MODE != MODE_P) {
         const float4 pa = W.prm[0][o], pb = W.prm[1][o];
         const float nn[3] = {pb.x, pb.y, pb.z};
         const float uu[3] = {pa.x, pa.y, pa.z};
@@ -559,7 +675,7 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
           const int o = owner_of(m);
           const float4 x = W.buf[w][0][lane], y = W.buf[w][1][lane];  // (v, tag), (r, pad)
           float v[3] = {x.x, x.y, x.z}, r[3] = {y.x, y.y, y.z};
-          const uint32_t c2 = advance(r, v, o);
+          const uint32_t c2 = advance(r, v, __float_as_uint(x.w), o);
           if (MODE == MODE_C) {
             store_rec(member(m, o), r, v, __float_as_uint(x.w));
           } else {
@@ -597,7 +713,7 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
           float r[3], w[3];
           uint32_t tag;
           load_rec(p, r, w, tag);
-          const uint32_t c2 = advance(r, w, lane);
+          const uint32_t c2 = advance(r, w, tag, lane);
           if (MODE == MODE_C) store_rec(p, r, w, tag);
           else emit(r, w, tag, c2, atomicAdd(&H.cnt_out[c2], 1u));
         }
@@ -605,43 +721,45 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS) ? 3 : 4) k_cells_warp
   }
 }
 
-template <bool TH, int MODE, bool FO, bool BE>
+template <bool TH, int MODE, bool FO, bool BE, bool AT>
 static void* warp_fn() {
-  return (void*)k_cells_warp<TH, MODE, FO, BE>;
+  return (void*)k_cells_warp<TH, MODE, FO, BE, AT>;
 }
 
 template <int MODE, bool BE>
-static void* warp_variant_mb(bool thermo, bool force) {
-  if (thermo) return force ? warp_fn<true, MODE, true, BE>() : warp_fn<true, MODE, false, BE>();
-  return force ? warp_fn<false, MODE, true, BE>() : warp_fn<false, MODE, false, BE>();
+static void* warp_variant_mb(bool thermo, bool force, bool at) {
+  if (at) return force ? warp_fn<false, MODE, true, BE, true>() : warp_fn<false, MODE, false, BE, true>();
+  if (thermo) return force ? warp_fn<true, MODE, true, BE, false>() : warp_fn<true, MODE, false, BE, false>();
+  return force ? warp_fn<false, MODE, true, BE, false>() : warp_fn<false, MODE, false, BE, false>();
 }
 
 template <int MODE>
-static void* warp_variant_mode(bool thermo, bool force, bool beads) {
-  return beads ? warp_variant_mb<MODE, true>(thermo, force) : warp_variant_mb<MODE, false>(thermo, force);
+static void* warp_variant_mode(bool thermo, bool force, bool beads, bool at) {
+  return beads ? warp_variant_mb<MODE, true>(thermo, force, at)
+               : warp_variant_mb<MODE, false>(thermo, force, at);
 }
 
-static void* warp_variant(bool thermo, bool force, bool beads, int mode) {
-  if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force, beads);
-  if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force, beads);
-  return warp_variant_mode<MODE_C>(thermo, force, beads);
+static void* warp_variant(bool thermo, bool force, bool beads, bool at, int mode) {
+  if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force, beads, at);
+  if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force, beads, at);
+  return warp_variant_mode<MODE_C>(thermo, force, beads, at);
 }
 
-int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, int mode) {
-  const void* fn = warp_variant(thermo, force, beads, mode);
-  const size_t smem = beads ? BLOCK_SMEM_BEADS : BLOCK_SMEM;
+int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode) {
+  const void* fn = warp_variant(thermo, force, beads, at, mode);
+  const size_t smem = block_smem(beads, at);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, smem);
   return nb;
 }
 
-void launch_cells_warp(bool thermo, bool force, bool beads, int mode, const BoxDev* boxes,
+void launch_cells_warp(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,
                        const int2* spans, int nspans, int grid, int* err, cudaStream_t s) {
   if (nspans <= 0) return;
   void* args[] = {(void*)&boxes, (void*)&spans, (void*)&nspans, (void*)&err};
-  cudaLaunchKernel(warp_variant(thermo, force, beads, mode), dim3(grid), dim3(BLOCK), args,
-                   beads ? BLOCK_SMEM_BEADS : BLOCK_SMEM, s);
+  cudaLaunchKernel(warp_variant(thermo, force, beads, at, mode), dim3(grid), dim3(BLOCK), args,
+                   block_smem(beads, at), s);
 }
 
 }  // namespace mpcd

@@ -19,6 +19,10 @@
 //            bound for the same cell share one slot atomic
 // Solute beads of the warp's bead group are handled one per lane with shared
 // per-cell sums.  The FP64 pipe bounds this kernel on GB300.
+//
+// The Andersen-thermostat variant (Eq. at, Sec. 3.7): pass 1 also sums each
+// member's Gaussian random velocity dv (drawn from its tag), the cell phase
+// forms the mass-weighted mean dbar, and pass 2 sets v = (u + dv) - dbar.
 #include "dev_collide.cuh"
 #include "dev_rows.cuh"
 #include "dev_stream.cuh"
@@ -62,6 +66,13 @@ struct BeadShared {  // per-cell bead sums (bead variants)
   int nb[32];
 };
 
+struct ATShared {  // Andersen rule: per-cell sums of dv, staged tags, bead sums of M dv
+  double D[3][32];
+  uint32_t tag[STAGE_PAD];
+  uint32_t pad_[4 - (STAGE_PAD & 3)];
+  double DX[3][32];
+};
+
 struct SpanParams {
   double dt, ca, sa, omc, m, Mb;
   double L[3], hg[3], gdt[3];
@@ -79,9 +90,13 @@ constexpr size_t SPAN_SMEM = (sizeof(SpanParams) + 15) & ~(size_t)15;
 constexpr size_t BLOCK_SMEM = SPAN_SMEM + WARPS * sizeof(WarpShared);
 constexpr size_t BLOCK_SMEM_BEADS = BLOCK_SMEM + WARPS * sizeof(BeadShared);
 
+__host__ __device__ constexpr size_t block_smem(bool beads, bool at) {
+  return BLOCK_SMEM + (beads ? WARPS * sizeof(BeadShared) : 0) + (at ? WARPS * sizeof(ATShared) : 0);
+}
+
 }  // namespace
 
-template <bool THERMO, int MODE, bool FORCE, bool BEADS>
+template <bool THERMO, int MODE, bool FORCE, bool BEADS, bool AT>
 __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restrict__ boxes,
                                                            const int2* __restrict__ spans,
                                                            int nspans, int* err) {
@@ -91,6 +106,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
   const int lane = threadIdx.x & 31;
   WarpShared& W = reinterpret_cast<WarpShared*>(smem_ + SPAN_SMEM)[threadIdx.x >> 5];
   BeadShared& BS = reinterpret_cast<BeadShared*>(smem_ + BLOCK_SMEM)[threadIdx.x >> 5];
+  ATShared& AS = reinterpret_cast<ATShared*>(smem_ + block_smem(BEADS, false))[threadIdx.x >> 5];
   const SpanParams& H = sp_;
   int box_of_params = -1;
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
@@ -162,10 +178,15 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
     auto stage = [&](int sbase, int cnt) {
       for (int j0 = 0; j0 < cnt; j0 += 64) {  // two windows of loads in flight
         double a[2][3];
+        uint32_t tg[2] = {0u, 0u};
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const int j = j0 + (u << 5) + lane;
-          if (j < cnt) load_v(member(sbase + j, owner_of(sbase + j)), a[u]);
+          if (j < cnt) {
+            const R* p = member(sbase + j, owner_of(sbase + j));
+            load_v(p, a[u]);
+            if (AT) tg[u] = p->tag;
+          }
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -175,6 +196,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
             W.sv[0][js] = a[u][0];
             W.sv[1][js] = a[u][1];
             W.sv[2][js] = a[u][2];
+            if (AT) AS.tag[js] = tg[u];
           }
         }
       }
@@ -199,21 +221,34 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
     if (MODE != MODE_P) {
       // ---- pass 1: momentum sums per cell (Sec. 3.5) ----
 #pragma unroll
-      for (int q = 0; q < 3; ++q) W.P[q][lane] = 0.0;
+      for (int q = 0; q < 3; ++q) {
+        W.P[q][lane] = 0.0;
+        if (AT) AS.D[q][lane] = 0.0;
+      }
       W.E[lane] = 0.0;
       __syncwarp();
       for (int sbase = 0; sbase < N; sbase += STAGE) {
         const int cnt = min(STAGE, N - sbase);
         stage(sbase, cnt);
-        double s[3] = {0.0, 0.0, 0.0};
+        double s[3] = {0.0, 0.0, 0.0}, sd[3] = {0.0, 0.0, 0.0};
         share(sbase, cnt, [&](int o, int js, bool last) {
 #pragma unroll
           for (int q = 0; q < 3; ++q) s[q] += W.sv[q][js];
+          if (AT) {  // Eq. at: this member's random velocity
+            double dv[3];
+            at_draw(B, t, AS.tag[js], 0u, B.sig, dv);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sd[q] += dv[q];
+          }
           if (last) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
               atomicAdd(&W.P[q][o], s[q]);
               s[q] = 0.0;
+              if (AT) {
+                atomicAdd(&AS.D[q][o], sd[q]);
+                sd[q] = 0.0;
+              }
             }
           }
         });
@@ -251,6 +286,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
       // ---- per cell: u = P / M, then the energy about u, axis and xi ----
       const bool occupied = n > 0 || nb > 0;
       double u[3] = {0.0, 0.0, 0.0};
+      double M = 1.0;
       if (occupied) {
         double Pv[3] = {W.P[0][lane], W.P[1][lane], W.P[2][lane]};
         if (has_ovf)
@@ -261,7 +297,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
 #pragma unroll
               for (int q = 0; q < 3; ++q) Pv[q] += w[q];
             }
-        const double M = (double)n * H.m + (double)nb * H.Mb;
+        M = (double)n * H.m + (double)nb * H.Mb;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           double P = H.m * Pv[q];
@@ -270,6 +306,56 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
         }
         W.pr[0][lane] = make_double2(u[0], u[1]);
         W.pr[1][lane] = make_double2(u[2], 1.0);
+      }
+      if (AT) {
+        // Eq. at: dbar = sum m dv / sum m over the cell's members and beads
+        if (BEADS && gnb > 0) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) AS.DX[q][lane] = 0.0;
+          __syncwarp();
+          for_beads([&](int j, int lc) {
+            double dv[3];
+            at_draw(B, t, B.border[j], 1u, B.sigb, dv);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) atomicAdd(&AS.DX[q][lc], H.Mb * dv[q]);
+          });
+          __syncwarp();
+        }
+        if (occupied) {
+          double Dv[3] = {AS.D[0][lane], AS.D[1][lane], AS.D[2][lane]};
+          if (has_ovf)
+            for (uint32_t j = 0; j < novf; ++j)
+              if (ovf_cell[j] == (uint32_t)cell) {
+                double dv[3];
+                at_draw(B, t, ovf[j].tag, 0u, B.sig, dv);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Dv[q] += dv[q];
+              }
+          double dbar[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            double D = H.m * Dv[q];
+            if (BEADS && gnb > 0) D += AS.DX[q][lane];
+            dbar[q] = D / M;
+          }
+          W.pr[0][lane] = make_double2(u[0], u[1]);
+          W.pr[1][lane] = make_double2(u[2], 0.0);
+          W.pr[2][lane] = make_double2(dbar[0], dbar[1]);
+          W.pr[3][lane] = make_double2(dbar[2], 0.0);
+        }
+        __syncwarp();
+        if (BEADS && gnb > 0) {  // Eq. at for the beads: v = (u + dv) - dbar
+          for_beads([&](int j, int lc) {
+            const double2 p0 = W.pr[0][lc], p1 = W.pr[1][lc], p2 = W.pr[2][lc], p3 = W.pr[3][lc];
+            const uint32_t b = B.border[j];
+            double dv[3];
+            at_draw(B, t, b, 1u, B.sigb, dv);
+            B.svel[3 * b] = (p0.x + dv[0]) - p2.x;
+            B.svel[3 * b + 1] = (p0.y + dv[1]) - p2.y;
+            B.svel[3 * b + 2] = (p1.x + dv[2]) - p3.x;
+          });
+        }
+        __syncwarp();
       }
       double xi = 1.0;
       if (THERMO) {
@@ -319,7 +405,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
           }
         }
       }
-      if (occupied) {
+      if (occupied && !AT) {
         double ax[3];
         axis_of(B, t, (uint32_t)cell, ax);  // Sec. 3.6
         W.pr[0][lane] = make_double2(u[0], u[1]);
@@ -328,7 +414,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
         W.pr[3][lane] = make_double2(ax[2], 0.0);
       }
       __syncwarp();
-      if (BEADS && gnb > 0) {  // collide the beads with their cell's parameters
+      if (BEADS && !AT && gnb > 0) {  // collide the beads with their cell's parameters
         for_beads([&](int j, int lc) {
           const double2 p0 = W.pr[0][lc], p1 = W.pr[1][lc], p2 = W.pr[2][lc], p3 = W.pr[3][lc];
           CellParams<double> prm;
@@ -346,8 +432,15 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
     }
 
     // ---- pass 2: collide (Eq. srd), stream (Eq. stream), bin (Sec. 3.4) ----
-    auto advance = [&](double r[3], double w[3], int o) -> uint32_t {
-      if (MODE != MODE_P) {
+    auto advance = [&](double r[3], double w[3], uint32_t tag, int o) -> uint32_t {
+      if (MODE != MODE_P && AT) {  // Eq. at
+        const double2 p0 = W.pr[0][o], p1 = W.pr[1][o], p2 = W.pr[2][o], p3 = W.pr[3][o];
+        double dv[3];
+        at_draw(B, t, tag, 0u, B.sig, dv);
+        w[0] = (p0.x + dv[0]) - p2.x;
+        w[1] = (p0.y + dv[1]) - p2.y;
+        w[2] = (p1.x + dv[2]) - p3.x;
+      } else if (MODE != MODE_P) {
         const double2 p0 = W.pr[0][o], p1 = W.pr[1][o], p2 = W.pr[2][o], p3 = W.pr[3][o];
         const double nn[3] = {p2.x, p2.y, p3.x};
         const double uu[3] = {p0.x, p0.y, p1.x};
@@ -418,7 +511,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
         r[0] = a.x; r[1] = a.y; r[2] = b.x;
         w[0] = b.y; w[1] = cq.x; w[2] = cq.y;
         tag = dq.x;
-        c2 = advance(r, w, o);
+        c2 = advance(r, w, tag, o);
         if (MODE == MODE_C) store_rec(member(m, o), r, w, tag);
       }
       if (MODE != MODE_C) {
@@ -440,7 +533,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
           double r[3], w[3];
           uint32_t tag;
           load_rec(p, r, w, tag);
-          const uint32_t c2 = advance(r, w, lane);
+          const uint32_t c2 = advance(r, w, tag, lane);
           if (MODE == MODE_C) store_rec(p, r, w, tag);
           else emit(r, w, tag, c2, atomicAdd(&H.cnt_out[c2], 1u));
         }
@@ -448,43 +541,44 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
   }
 }
 
-template <bool TH, int MODE, bool FO, bool BE>
+template <bool TH, int MODE, bool FO, bool BE, bool AT>
 static void* warpd_fn() {
-  return (void*)k_cells_warp_d<TH, MODE, FO, BE>;
+  return (void*)k_cells_warp_d<TH, MODE, FO, BE, AT>;
 }
 
 template <int MODE, bool BE>
-static void* warpd_variant_mb(bool thermo, bool force) {
-  if (thermo) return force ? warpd_fn<true, MODE, true, BE>() : warpd_fn<true, MODE, false, BE>();
-  return force ? warpd_fn<false, MODE, true, BE>() : warpd_fn<false, MODE, false, BE>();
+static void* warpd_variant_mb(bool thermo, bool force, bool at) {
+  if (at) return force ? warpd_fn<false, MODE, true, BE, true>() : warpd_fn<false, MODE, false, BE, true>();
+  if (thermo) return force ? warpd_fn<true, MODE, true, BE, false>() : warpd_fn<true, MODE, false, BE, false>();
+  return force ? warpd_fn<false, MODE, true, BE, false>() : warpd_fn<false, MODE, false, BE, false>();
 }
 
-static void* warpd_variant(bool thermo, bool force, bool beads, int mode) {
+static void* warpd_variant(bool thermo, bool force, bool beads, bool at, int mode) {
   if (mode == MODE_P)
-    return beads ? warpd_variant_mb<MODE_P, true>(thermo, force)
-                 : warpd_variant_mb<MODE_P, false>(thermo, force);
+    return beads ? warpd_variant_mb<MODE_P, true>(thermo, force, at)
+                 : warpd_variant_mb<MODE_P, false>(thermo, force, at);
   if (mode == MODE_F)
-    return beads ? warpd_variant_mb<MODE_F, true>(thermo, force)
-                 : warpd_variant_mb<MODE_F, false>(thermo, force);
-  return beads ? warpd_variant_mb<MODE_C, true>(thermo, force)
-               : warpd_variant_mb<MODE_C, false>(thermo, force);
+    return beads ? warpd_variant_mb<MODE_F, true>(thermo, force, at)
+                 : warpd_variant_mb<MODE_F, false>(thermo, force, at);
+  return beads ? warpd_variant_mb<MODE_C, true>(thermo, force, at)
+               : warpd_variant_mb<MODE_C, false>(thermo, force, at);
 }
 
-int cells_warpd_blocks_per_sm(bool thermo, bool force, bool beads, int mode) {
-  const void* fn = warpd_variant(thermo, force, beads, mode);
-  const size_t smem = beads ? BLOCK_SMEM_BEADS : BLOCK_SMEM;
+int cells_warpd_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode) {
+  const void* fn = warpd_variant(thermo, force, beads, at, mode);
+  const size_t smem = block_smem(beads, at);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, smem);
   return nb;
 }
 
-void launch_cells_warpd(bool thermo, bool force, bool beads, int mode, const BoxDev* boxes,
+void launch_cells_warpd(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,
                         const int2* spans, int nspans, int grid, int* err, cudaStream_t s) {
   if (nspans <= 0) return;
   void* args[] = {(void*)&boxes, (void*)&spans, (void*)&nspans, (void*)&err};
-  cudaLaunchKernel(warpd_variant(thermo, force, beads, mode), dim3(grid), dim3(BLOCK), args,
-                   beads ? BLOCK_SMEM_BEADS : BLOCK_SMEM, s);
+  cudaLaunchKernel(warpd_variant(thermo, force, beads, at, mode), dim3(grid), dim3(BLOCK), args,
+                   block_smem(beads, at), s);
 }
 
 }  // namespace mpcd

@@ -16,14 +16,16 @@ void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const 
 // The same step for mixed-model boxes without walls, members spread over the
 // lanes of a warp (k_cells_warp.cu); valid for row capacities up to
 // WARP_MAX_K and boxes below 2^22 cells per axis.  force: nonzero body force;
-// beads: the box has solute beads.
+// beads: the box has solute beads; at: Andersen-thermostat rule (Eq. at)
+// instead of the rotation (thermo is then false).  The Andersen rule runs
+// only on these kernels.
 constexpr int WARP_MAX_K = 448;
-int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, int mode);
-void launch_cells_warp(bool thermo, bool force, bool beads, int mode, const BoxDev* boxes,
+int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode);
+void launch_cells_warp(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,
                        const int2* spans, int nspans, int grid, int* err, cudaStream_t s);
 // The FP64 model's counterpart (k_cells_warp_d.cu), same conditions.
-int cells_warpd_blocks_per_sm(bool thermo, bool force, bool beads, int mode);
-void launch_cells_warpd(bool thermo, bool force, bool beads, int mode, const BoxDev* boxes,
+int cells_warpd_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode);
+void launch_cells_warpd(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,
                         const int2* spans, int nspans, int grid, int* err, cudaStream_t s);
 // Place n particles (device arrays of float (mixed) or double, n x 3) in the
 // current rows of a box whose counts are zero.

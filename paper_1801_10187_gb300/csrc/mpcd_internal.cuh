@@ -27,6 +27,11 @@ constexpr uint32_t PURPOSE_SHIFT = 0x53484654u;
 constexpr uint32_t PURPOSE_ROT = 0x524F5441u;
 constexpr uint32_t PURPOSE_THERMO = 0x54484D4Fu;
 constexpr uint32_t PURPOSE_VIRT = 0x56495254u;
+constexpr uint32_t PURPOSE_AT = 0x414E4452u;
+
+// Collision rules: stochastic rotation (Eq. srd) or Andersen thermostat (Eq. at).
+constexpr int RULE_SRD = 0;
+constexpr int RULE_AT = 1;
 
 // Error bits raised by kernels (read back by the host at sync points).
 constexpr int ERR_GAMMA_CAP = 1;   // thermostat sampler rejected 64 times
@@ -99,7 +104,11 @@ struct BoxDev {
   // updated on the device
   unsigned long long step;
   int32_t cur;
-  int32_t pad_i;
+  int32_t collision;    // RULE_SRD or RULE_AT
+  // Andersen rule: standard deviation sqrt(kT/m) of a random velocity
+  // component, solvent and beads
+  double sig, sigb;
+  float sig_f, sigb_f;
 };
 
 // Segments for the segmented exclusive scan (cells of each box, and bead

@@ -1,0 +1,139 @@
+"""GPU parity at the full sizes of the benchmark workloads, in the launch
+configuration the benchmark times (captured graphs of the fused pass, one
+launch per step), against the oracle run on the same states.
+
+  * 100^3 cells at density 10 (10^7 particles), mixed and FP64, and the
+    Andersen-rule variant of the mixed box: two steps (the stream/bin pass,
+    one fused collide + stream/bin pass, and the completing collision), every
+    particle compared.
+  * 250^3 cells at density 5 (7.8 * 10^7 particles) with 2000 chains of 50
+    beads and the cell thermostat: two steps, every particle compared.
+  * the 64-box ensemble (about 1.5 * 10^8 particles) stepped in one batch:
+    three boxes compared particle by particle, and for every box the
+    momentum conservation that holds at any size.
+Tolerances as in the small parity tests: mixed bit-exact, FP64 1e-12
+relative per step.  These runs take a few minutes of oracle time.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_10187_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+import paper_1801_10187_gb300 as pkg  # noqa: E402
+
+W = inputs.WORKLOADS
+
+
+def rel_err(v, ref, kT=1.0, m=1.0):
+    scale = np.maximum(np.linalg.norm(ref, axis=1), math.sqrt(kT / m))
+    return (np.linalg.norm(v - ref, axis=1) / scale).max(initial=0.0)
+
+
+def box_kw(cfg):
+    kw = dict(n=cfg["n"], dt=cfg["dt"], alpha_deg=cfg["alpha_deg"], kT=cfg["kT"],
+              seed=cfg["seed"], thermostat=cfg["thermostat"], precision=cfg["precision"],
+              collision=cfg.get("collision", "srd"))
+    if cfg.get("n_chains"):
+        kw.update(chain_len=cfg["chain_len"], md_substeps=cfg["md_substeps"],
+                  solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"])
+    return kw
+
+
+def oracle_params(kw):
+    return oracle.Params(
+        n=kw["n"], dt=kw["dt"], alpha_deg=kw["alpha_deg"], kT=kw["kT"], seed=kw["seed"],
+        thermostat=kw["thermostat"],
+        precision=oracle.MIXED if kw["precision"] == "mixed" else oracle.FP64,
+        collision=oracle.AT if kw["collision"] == "at" else oracle.SRD,
+        chain_len=kw.get("chain_len", 0), md_substeps=kw.get("md_substeps", 0),
+        solute_mass=kw.get("solute_mass", 1.0), bond_k=kw.get("bond_k", 0.0),
+        bond_r0=kw.get("bond_r0", 0.0))
+
+
+def run_full(name, steps=2):
+    cfg = W[name]
+    kw = box_kw(cfg)
+    mixed = cfg["precision"] == "mixed"
+    s = inputs.solvent(cfg["n"], cfg["density"], kT=cfg["kT"], seed=cfg["seed"], mixed=mixed)
+    sp = sv = None
+    if cfg.get("n_chains"):
+        sp, sv = inputs.chains(cfg["n"], cfg["n_chains"], cfg["chain_len"], cfg["bond_r0"],
+                               kT=cfg["kT"], bead_mass=cfg["bead_mass"], seed=cfg["seed"] + 1000)
+    box = pkg.Box(**kw)
+    box.set_state(s.pos, s.vel, sp, sv)
+    box.step(steps)
+    pos, vel, spos, svel, st = box.get_state()
+    cells, counts = box.last_cells()
+    box.close()
+    ref = oracle.State(np.asarray(s.pos, np.float64), np.asarray(s.vel, np.float64),
+                       np.zeros((0, 3)) if sp is None else sp.copy(),
+                       np.zeros((0, 3)) if sv is None else sv.copy())
+    del s
+    rc, rk = oracle.step(oracle_params(kw), ref, steps, want_cells=True)
+    assert st == ref.step == steps
+    np.testing.assert_array_equal(cells, rc)
+    np.testing.assert_array_equal(counts, rk)
+    if mixed:
+        np.testing.assert_array_equal(pos, ref.pos)
+        np.testing.assert_array_equal(vel, ref.vel)
+    else:
+        assert rel_err(vel, ref.vel) <= 1e-12 * steps
+        assert np.max(np.abs(pos - ref.pos)) <= 1e-10
+    return spos, svel, ref
+
+
+@pytest.mark.parametrize("name", ["srd-100c-rho10-mixed", "srd-100c-rho10-fp64",
+                                  "srd-100c-rho10-mixed-at"])
+def test_fullsize_10m(name):
+    run_full(name)
+
+
+def test_fullsize_78m_solute_thermostat():
+    spos, svel, ref = run_full("srd-250c-rho5-mixed-solute")
+    assert rel_err(svel, ref.svel, m=5.0) == 0.0
+    assert np.max(np.abs(spos - ref.spos)) <= 1e-11
+
+
+def test_fullsize_batch64():
+    cfg = W["srd-batch64-mixed"]
+    specs = inputs.ensemble(cfg["n_boxes"], seed=cfg["ensemble_seed"])
+    counts = [int(round(s["density"] * np.prod(s["n"]))) for s in specs]
+    batch = pkg.Batch(cfg["precision"])
+    slots = []
+    for s, n in zip(specs, counts):
+        slots.append(batch.add_thermal(n, init_seed=s["seed"], n=s["n"], alpha_deg=s["alpha_deg"],
+                                       seed=s["seed"], dt=cfg["dt"], kT=cfg["kT"],
+                                       thermostat=cfg["thermostat"]))
+    order = np.argsort(counts)
+    picked = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    start = {i: batch.get_state(slots[i]) for i in picked}
+    ob0 = [batch.observables(sl) for sl in slots]
+    steps = 2
+    batch.step(steps)
+    P1 = [batch.observables(sl)["P"] for sl in slots]
+    got = {i: batch.get_state(slots[i]) for i in picked}
+    batch.close()
+    for i in picked:
+        s = specs[i]
+        p = oracle.Params(n=s["n"], dt=cfg["dt"], alpha_deg=s["alpha_deg"], kT=cfg["kT"],
+                          seed=s["seed"], thermostat=cfg["thermostat"], precision=oracle.MIXED)
+        ref = oracle.State(start[i][0].copy(), start[i][1].copy())
+        oracle.step(p, ref, steps)
+        np.testing.assert_array_equal(got[i][0], ref.pos)
+        np.testing.assert_array_equal(got[i][1], ref.vel)
+        assert got[i][2] == steps
+    # every box: momentum conserved by the collisions up to the float rounding
+    # of each stored velocity, |dP| <= steps 2^-24 sum |v| <= steps 2^-24
+    # sqrt(2 n KE) (unit mass)
+    for n, o, b in zip(counts, ob0, P1):
+        bound = steps * 2.0**-24 * math.sqrt(2.0 * n * o["KE"])
+        assert np.max(np.abs(o["P"] - b)) <= bound
