@@ -154,6 +154,25 @@ __device__ __forceinline__ float series_log(float x) {
   return (e >= 0 ? small_to_float(e) : -small_to_float(-e)) * ln2 + (2.0f * t) * series;
 }
 
+// series_log for 2^-32 <= x <= 1 (a normal positive float): the same
+// operations without the special cases.
+__device__ __forceinline__ float series_log_unit(float x) {
+  uint32_t b = __float_as_uint(x);
+  int e = (int)((b >> 23) & 0xFFu) - 127;
+  float m = __uint_as_float((b & 0x7FFFFFu) | 0x3F800000u);
+  if (m > 1.41421354f) {
+    m = m * 0.5f;
+    e += 1;
+  }
+  const float t = (m - 1.0f) / (m + 1.0f);
+  const float t2 = t * t;
+  const float l3 = (float)(1.0 / 3.0), l5 = (float)(1.0 / 5.0), l7 = (float)(1.0 / 7.0);
+  const float l9 = (float)(1.0 / 9.0), l11 = (float)(1.0 / 11.0);
+  const float series = 1.0f + t2 * (l3 + t2 * (l5 + t2 * (l7 + t2 * (l9 + t2 * l11))));
+  const float ln2 = (float)0.69314718055994530942;
+  return (e >= 0 ? small_to_float(e) : -small_to_float(-e)) * ln2 + (2.0f * t) * series;
+}
+
 __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, uint32_t cell,
                                         float n[3]) {
   const uint4 w = draw(B, PURPOSE_ROT, cell, 0u, t);
@@ -252,8 +271,8 @@ __device__ __forceinline__ void at_draw(const BoxDev& B, unsigned long long t, u
   const uint4 w = draw(B, PURPOSE_AT, tag, 2u * kind, t);
   const float e1 = comp_word_to_float(w.x) * 0x1p-32f;  // 1 - U in (0, 1]
   const float e2 = comp_word_to_float(w.z) * 0x1p-32f;
-  const float r1 = sqrtf(-2.0f * series_log(e1));
-  const float r2 = sqrtf(-2.0f * series_log(e2));
+  const float r1 = sqrtf(-2.0f * series_log_unit(e1));
+  const float r2 = sqrtf(-2.0f * series_log_unit(e2));
   float c1, s1, c2, s2;
   turn_cos_sin(w.y, c1, s1);
   turn_cos_sin(w.w, c2, s2);
@@ -269,8 +288,10 @@ __device__ __forceinline__ void at_draw(const BoxDev& B, unsigned long long t, u
   const double U1 = unit53(wa.x, wb.x), U2 = unit53(wa.y, wb.y);
   const double U3 = unit53(wa.z, wb.z), U4 = unit53(wa.w, wb.w);
   const double r1 = sqrt(-2.0 * log(1.0 - U1)), r2 = sqrt(-2.0 * log(1.0 - U3));
-  dv[0] = sigma * (r1 * cos(kTwoPi * U2));
-  dv[1] = sigma * (r1 * sin(kTwoPi * U2));
+  double s1, c1;
+  sincos(kTwoPi * U2, &s1, &c1);  // one argument reduction for the pair
+  dv[0] = sigma * (r1 * c1);
+  dv[1] = sigma * (r1 * s1);
   dv[2] = sigma * (r2 * cos(kTwoPi * U4));
 }
 

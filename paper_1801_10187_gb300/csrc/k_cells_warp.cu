@@ -85,14 +85,20 @@ struct BeadShared {
 };
 
 // Andersen-rule accumulators of one warp: split sums of the random
-// velocities per cell, the tags of the staged members, and the beads' exact
-// int64 random momenta.
+// velocities per cell, the tags of the staged members, the beads' exact int64
+// random momenta, and the random velocities of the first DV_CAP members
+// (index m + m / 32), drawn once in pass 1 and used again in pass 2.  Members
+// beyond DV_CAP draw theirs again in pass 2.
+template <int DV_CAP>
 struct ATShared {
   int h[3][32];
   int l[3][32];
   uint32_t tag[STAGE_PAD];
   unsigned long long DX[3][32];
+  float dv[3][DV_CAP + DV_CAP / 32];
 };
+constexpr int DV_CAP = 448;        // cached members per warp
+constexpr int DV_CAP_BEADS = 320;  // with the bead accumulators (two blocks per SM fit)
 
 // Shared memory of one block: the span parameters, then one area per warp;
 // kept under 48 KB so that four blocks (the register limit) fit on an SM with
@@ -126,7 +132,8 @@ constexpr size_t BLOCK_SMEM = SPAN_SMEM + WARPS * WARP_SMEM;
 constexpr size_t BLOCK_SMEM_BEADS = BLOCK_SMEM + WARPS * sizeof(BeadShared);
 
 __host__ __device__ constexpr size_t block_smem(bool beads, bool at) {
-  return BLOCK_SMEM + (beads ? WARPS * sizeof(BeadShared) : 0) + (at ? WARPS * sizeof(ATShared) : 0);
+  return BLOCK_SMEM + (beads ? WARPS * sizeof(BeadShared) : 0) +
+         (at ? WARPS * (beads ? sizeof(ATShared<DV_CAP_BEADS>) : sizeof(ATShared<DV_CAP>)) : 0);
 }
 
 // floor(x - s) for 0 <= x < 2^22 and s = S 2^-32 in [-1/2, 1/2), exactly:
@@ -161,11 +168,13 @@ __device__ __forceinline__ float wrap_fast(float x, float L) {
 
 }  // namespace
 
-// Thermostat, bead and Andersen variants keep more values live through the
-// per-cell phase; they run three blocks per SM with 80 registers instead of
-// spilling.  AT selects the Andersen rule (then THERMO is false).
+// Thermostat and bead variants keep more values live through the per-cell
+// phase; they run three blocks per SM with 80 registers instead of spilling.
+// AT selects the Andersen rule (then THERMO is false): its two Box-Muller
+// draws per member want registers for independent chains, and its cache of
+// random velocities wants shared memory, so it runs two blocks per SM.
 template <bool THERMO, int MODE, bool FORCE, bool BEADS, bool AT>
-__global__ void __launch_bounds__(BLOCK, (THERMO || BEADS || AT) ? 3 : 4) k_cells_warp(const BoxDev* __restrict__ boxes,
+__global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k_cells_warp(const BoxDev* __restrict__ boxes,
                                                          const int2* __restrict__ spans,
                                                          int nspans, int* err) {
   using R = RecF;
@@ -175,7 +184,8 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS || AT) ? 3 : 4) k_cell
   WarpShared& W =
       reinterpret_cast<WarpShared*>(smem_ + SPAN_SMEM)[threadIdx.x >> 5];
   BeadShared& BS = reinterpret_cast<BeadShared*>(smem_ + BLOCK_SMEM)[threadIdx.x >> 5];
-  ATShared& AS = reinterpret_cast<ATShared*>(smem_ + block_smem(BEADS, false))[threadIdx.x >> 5];
+  constexpr int DVC = BEADS ? DV_CAP_BEADS : DV_CAP;
+  ATShared<DVC>& AS = reinterpret_cast<ATShared<DVC>*>(smem_ + block_smem(BEADS, false))[threadIdx.x >> 5];
   const SpanParams& H = sp_;
   int box_of_params = -1;  // the span parameters depend on the box only
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
@@ -272,6 +282,20 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS || AT) ? 3 : 4) k_cell
             if (AT) AS.tag[js] = __float_as_uint(a[u].w);
           }
         }
+        if (AT && MODE != MODE_P) {  // Eq. at: random velocities of the cached members
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j0 + (u << 5) + lane, m = sbase + j;
+            if (j < cnt && m < DVC) {
+              float dv[3];
+              at_draw(B, t, __float_as_uint(a[u].w), 0u, B.sig_f, dv);
+              const int mp = m + (m >> 5);
+              AS.dv[0][mp] = dv[0];
+              AS.dv[1][mp] = dv[1];
+              AS.dv[2][mp] = dv[2];
+            }
+          }
+        }
       }
       __syncwarp();
     };
@@ -326,7 +350,14 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS || AT) ? 3 : 4) k_cell
           }
           if (AT) {  // Eq. at: this member's random velocity, summed the same way
             float dv[3];
-            at_draw(B, t, AS.tag[js], 0u, B.sig_f, dv);
+            const int mp = sbase + (sbase >> 5) + js;  // padded member index
+            if (sbase + js - js / 33 < DVC) {  // js = j + j / 32, so j = js - js / 33
+              dv[0] = AS.dv[0][mp];
+              dv[1] = AS.dv[1][mp];
+              dv[2] = AS.dv[2][mp];
+            } else {
+              at_draw(B, t, AS.tag[js], 0u, B.sig_f, dv);
+            }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
               int h, l;
@@ -581,11 +612,23 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS || AT) ? 3 : 4) k_cell
 
     // ---- pass 2: collide (Eq. srd), stream (Eq. stream), bin (Sec. 3.4) ----
     // new state of a member and its cell for the next step
-    auto advance = [&](float r[3], float w[3], uint32_t tag, int o) -> uint32_t {
+    // Eq. at: member m's random velocity, from the cache or drawn again (m < 0:
+    // an overflow member)
+    auto at_dv = [&](int m, uint32_t tag, float dv[3]) {
+      if (m >= 0 && m < DVC) {
+        const int mp = m + (m >> 5);
+        dv[0] = AS.dv[0][mp];
+        dv[1] = AS.dv[1][mp];
+        dv[2] = AS.dv[2][mp];
+      } else {
+        at_draw(B, t, tag, 0u, B.sig_f, dv);
+      }
+    };
+    auto advance = [&](float r[3], float w[3], uint32_t tag, int o, int m) -> uint32_t {
       if (MODE != MODE_P && AT) {  // Eq. at
         const float4 pa = W.prm[0][o], pb = W.prm[1][o];
         float dv[3];
-        at_draw(B, t, tag, 0u, B.sig_f, dv);
+        at_dv(m, tag, dv);
         w[0] = (pa.x + dv[0]) - pb.x;
         w[1] = (pa.y + dv[1]) - pb.y;
         w[2] = (pa.z + dv[2]) - pb.z;
@@ -675,7 +718,7 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS || AT) ? 3 : 4) k_cell
           const int o = owner_of(m);
           const float4 x = W.buf[w][0][lane], y = W.buf[w][1][lane];  // (v, tag), (r, pad)
           float v[3] = {x.x, x.y, x.z}, r[3] = {y.x, y.y, y.z};
-          const uint32_t c2 = advance(r, v, __float_as_uint(x.w), o);
+          const uint32_t c2 = advance(r, v, __float_as_uint(x.w), o, m);
           if (MODE == MODE_C) {
             store_rec(member(m, o), r, v, __float_as_uint(x.w));
           } else {
@@ -713,7 +756,7 @@ __global__ void __launch_bounds__(BLOCK, (THERMO || BEADS || AT) ? 3 : 4) k_cell
           float r[3], w[3];
           uint32_t tag;
           load_rec(p, r, w, tag);
-          const uint32_t c2 = advance(r, w, tag, lane);
+          const uint32_t c2 = advance(r, w, tag, lane, -1);
           if (MODE == MODE_C) store_rec(p, r, w, tag);
           else emit(r, w, tag, c2, atomicAdd(&H.cnt_out[c2], 1u));
         }
