@@ -63,6 +63,8 @@ class _Params(ctypes.Structure):
         ("solute_mass", ctypes.c_double),
         ("bond_k", ctypes.c_double),
         ("bond_r0", ctypes.c_double),
+        ("angular", ctypes.c_int32),
+        ("pad2_", ctypes.c_int32),
     ]
 
 
@@ -117,6 +119,7 @@ class Params:
     bond_k: float = 0.0
     bond_r0: float = 0.0
     collision: int = SRD
+    angular: bool = False
 
     def c(self) -> _Params:
         p = _Params()
@@ -137,6 +140,7 @@ class Params:
         p.bond_k = self.bond_k
         p.bond_r0 = self.bond_r0
         p.collision = int(self.collision)
+        p.angular = int(bool(self.angular))
         return p
 
 

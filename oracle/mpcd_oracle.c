@@ -499,6 +499,201 @@ static void virtual_velocity(const oracle_params* p, uint64_t t, uint32_t cell, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Angular-momentum conservation (Sec. 2: the rules conserve linear momentum */
+/* only; the paper cites Noguchi & Gompper for the constraint that restores  */
+/* angular momentum).  After the collision rule, every member of a cell      */
+/* receives omega x r_c, where r_c is its position relative to the cell's    */
+/* centre of mass and omega solves Pi omega = dL with                        */
+/* dL = sum m r_c x (v - v') (v before, v' after the rule) and the inertia    */
+/* tensor Pi = sum m (|r_c|^2 I - r_c r_c^T): the cell's angular momentum    */
+/* about its centre of mass is then what it was before the collision, and    */
+/* its linear momentum is unchanged (sum m r_c = 0).  Positions are taken    */
+/* in the frame of the shifted cell (rel_pos, in [0, 1) per axis).  A cell   */
+/* of two members (or with all members on a line) has an inertia tensor of  */
+/* rank two; there omega = 2 dL / tr(Pi), which solves the system on the    */
+/* plane normal to the line (dL has no component along it).  The mixed       */
+/* model sums in int64 fixed point (scale 2^32) and solves in float.         */
+/* ------------------------------------------------------------------------ */
+static double rel_pos(const oracle_params* p, double x, double s, int64_t i, int k) {
+  double d = (x - s) - (double)i;
+  double L = (double)p->n[k];
+  if (d < 0.0) d += L;
+  else if (d >= 1.0) d -= L;
+  return d;
+}
+
+static void cell_coords(const oracle_params* p, int32_t c, int64_t ic[3]) {
+  int64_t nx = p->n[0], ny = p->n[1];
+  ic[0] = c % nx;
+  ic[1] = (c / nx) % ny;
+  ic[2] = c / (nx * ny);
+}
+
+/* omega from Pi omega = dL, Pi = [[a, b, c], [b, d, e], [c, e, f]] (float). */
+static void solve_omega_f(int32_t nc, const float P[6], const float dL[3], float w[3]) {
+  float a = P[0], b = P[1], c = P[2], d = P[3], e = P[4], f = P[5];
+  float A = d * f - e * e, B = c * e - b * f, C = b * e - c * d;
+  float D = a * f - c * c, E = b * c - a * e, F = a * d - b * b;
+  float det = a * A + b * B + c * C;
+  float tr = a + d + f;
+  float t3 = tr / 3.0f;
+  if (nc >= 3 && det > 1e-6f * (t3 * t3 * t3)) {
+    w[0] = (A * dL[0] + B * dL[1] + C * dL[2]) / det;
+    w[1] = (B * dL[0] + D * dL[1] + E * dL[2]) / det;
+    w[2] = (C * dL[0] + E * dL[1] + F * dL[2]) / det;
+  } else if (tr > 0.0f) {
+    float g = 2.0f / tr;
+    for (int k = 0; k < 3; ++k) w[k] = dL[k] * g;
+  } else {
+    w[0] = w[1] = w[2] = 0.0f;
+  }
+}
+
+static void solve_omega_d(int32_t nc, const double P[6], const double dL[3], double w[3]) {
+  double a = P[0], b = P[1], c = P[2], d = P[3], e = P[4], f = P[5];
+  double A = d * f - e * e, B = c * e - b * f, C = b * e - c * d;
+  double D = a * f - c * c, E = b * c - a * e, F = a * d - b * b;
+  double det = a * A + b * B + c * C;
+  double tr = a + d + f;
+  double t3 = tr / 3.0;
+  if (nc >= 3 && det > 1e-6 * (t3 * t3 * t3)) {
+    w[0] = (A * dL[0] + B * dL[1] + C * dL[2]) / det;
+    w[1] = (B * dL[0] + D * dL[1] + E * dL[2]) / det;
+    w[2] = (C * dL[0] + E * dL[1] + F * dL[2]) / det;
+  } else if (tr > 0.0) {
+    double g = 2.0 / tr;
+    for (int k = 0; k < 3; ++k) w[k] = dL[k] * g;
+  } else {
+    w[0] = w[1] = w[2] = 0.0;
+  }
+}
+
+/* v0: velocities before the collision, vel: after it (corrected in place). */
+static void angular_correction(const oracle_params* p, int64_t n, const double* pos,
+                               const double* v0, double* vel, const int32_t* cellid,
+                               const double s[3], int64_t ncells, const int32_t* cnt) {
+  const int mixed = (p->precision == ORACLE_MIXED);
+  const double m = p->mass;
+  const float mf = (float)m;
+  int64_t* Q = (int64_t*)calloc((size_t)ncells * 3, sizeof(int64_t));
+  int64_t* Lq = (int64_t*)calloc((size_t)ncells * 3, sizeof(int64_t));
+  int64_t* Pq = (int64_t*)calloc((size_t)ncells * 6, sizeof(int64_t));
+  double* Qd = (double*)calloc((size_t)ncells * 3, sizeof(double));
+  double* Ldd = (double*)calloc((size_t)ncells * 3, sizeof(double));
+  double* Pdd = (double*)calloc((size_t)ncells * 6, sizeof(double));
+  double* rcm = (double*)calloc((size_t)ncells * 3, sizeof(double));
+  double* om = (double*)calloc((size_t)ncells * 3, sizeof(double));
+  /* positions relative to the shifted cell, one member at a time */
+  #define REL(i, r)                                                       \
+    do {                                                                  \
+      int64_t ic_[3];                                                     \
+      cell_coords(p, cellid[i], ic_);                                     \
+      for (int k_ = 0; k_ < 3; ++k_)                                      \
+        r[k_] = rel_pos(p, pos[3 * (i) + k_], s[k_], ic_[k_], k_);        \
+    } while (0)
+  /* centre of mass of each cell */
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t c = cellid[i];
+    double r[3];
+    REL(i, r);
+    for (int k = 0; k < 3; ++k) {
+      if (mixed) Q[3 * c + k] += llrint((double)(float)r[k] * 0x1p32);
+      else Qd[3 * c + k] += r[k];
+    }
+  }
+  for (int64_t c = 0; c < ncells; ++c) {
+    if (cnt[c] == 0) continue;
+    for (int k = 0; k < 3; ++k) {
+      if (mixed) rcm[3 * c + k] = (double)(((float)Q[3 * c + k] * 0x1p-32f) / (float)cnt[c]);
+      else rcm[3 * c + k] = Qd[3 * c + k] / (double)cnt[c];
+    }
+  }
+  /* dL = sum m r_c x (v - v') and the inertia tensor */
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t c = cellid[i];
+    double r[3];
+    REL(i, r);
+    if (mixed) {
+      float rc[3], dv[3], x[3], t[6];
+      for (int k = 0; k < 3; ++k) {
+        rc[k] = (float)r[k] - (float)rcm[3 * c + k];
+        dv[k] = (float)v0[3 * i + k] - (float)vel[3 * i + k];
+      }
+      x[0] = rc[1] * dv[2] - rc[2] * dv[1];
+      x[1] = rc[2] * dv[0] - rc[0] * dv[2];
+      x[2] = rc[0] * dv[1] - rc[1] * dv[0];
+      t[0] = rc[1] * rc[1] + rc[2] * rc[2];
+      t[1] = rc[0] * rc[1];
+      t[2] = rc[0] * rc[2];
+      t[3] = rc[0] * rc[0] + rc[2] * rc[2];
+      t[4] = rc[1] * rc[2];
+      t[5] = rc[0] * rc[0] + rc[1] * rc[1];
+      for (int k = 0; k < 3; ++k) Lq[3 * c + k] += llrint((double)x[k] * 0x1p32);
+      for (int k = 0; k < 6; ++k) Pq[6 * c + k] += llrint((double)t[k] * 0x1p32);
+    } else {
+      double rc[3], dv[3];
+      for (int k = 0; k < 3; ++k) {
+        rc[k] = r[k] - rcm[3 * c + k];
+        dv[k] = v0[3 * i + k] - vel[3 * i + k];
+      }
+      Ldd[3 * c + 0] += m * (rc[1] * dv[2] - rc[2] * dv[1]);
+      Ldd[3 * c + 1] += m * (rc[2] * dv[0] - rc[0] * dv[2]);
+      Ldd[3 * c + 2] += m * (rc[0] * dv[1] - rc[1] * dv[0]);
+      Pdd[6 * c + 0] += m * (rc[1] * rc[1] + rc[2] * rc[2]);
+      Pdd[6 * c + 1] -= m * (rc[0] * rc[1]);
+      Pdd[6 * c + 2] -= m * (rc[0] * rc[2]);
+      Pdd[6 * c + 3] += m * (rc[0] * rc[0] + rc[2] * rc[2]);
+      Pdd[6 * c + 4] -= m * (rc[1] * rc[2]);
+      Pdd[6 * c + 5] += m * (rc[0] * rc[0] + rc[1] * rc[1]);
+    }
+  }
+  /* omega of each cell */
+  for (int64_t c = 0; c < ncells; ++c) {
+    if (cnt[c] == 0) continue;
+    if (mixed) {
+      float P[6], dL[3], w[3];
+      for (int k = 0; k < 3; ++k) dL[k] = mf * ((float)Lq[3 * c + k] * 0x1p-32f);
+      for (int k = 0; k < 6; ++k) {
+        float e = mf * ((float)Pq[6 * c + k] * 0x1p-32f);
+        P[k] = (k == 1 || k == 2 || k == 4) ? -e : e;
+      }
+      solve_omega_f(cnt[c], P, dL, w);
+      for (int k = 0; k < 3; ++k) om[3 * c + k] = (double)w[k];
+    } else {
+      solve_omega_d(cnt[c], &Pdd[6 * c], &Ldd[3 * c], &om[3 * c]);
+    }
+  }
+  /* v'' = v' + omega x r_c */
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t c = cellid[i];
+    double r[3];
+    REL(i, r);
+    if (mixed) {
+      float rc[3], w[3];
+      for (int k = 0; k < 3; ++k) {
+        rc[k] = (float)r[k] - (float)rcm[3 * c + k];
+        w[k] = (float)om[3 * c + k];
+      }
+      float a0 = w[1] * rc[2] - w[2] * rc[1];
+      float a1 = w[2] * rc[0] - w[0] * rc[2];
+      float a2 = w[0] * rc[1] - w[1] * rc[0];
+      vel[3 * i + 0] = (double)((float)vel[3 * i + 0] + a0);
+      vel[3 * i + 1] = (double)((float)vel[3 * i + 1] + a1);
+      vel[3 * i + 2] = (double)((float)vel[3 * i + 2] + a2);
+    } else {
+      double rc[3];
+      const double* w = &om[3 * c];
+      for (int k = 0; k < 3; ++k) rc[k] = r[k] - rcm[3 * c + k];
+      vel[3 * i + 0] += w[1] * rc[2] - w[2] * rc[1];
+      vel[3 * i + 1] += w[2] * rc[0] - w[0] * rc[2];
+      vel[3 * i + 2] += w[0] * rc[1] - w[1] * rc[0];
+    }
+  }
+  #undef REL
+  free(Q); free(Lq); free(Pq); free(Qd); free(Ldd); free(Pdd); free(rcm); free(om);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 2 Eq. (srd) written as a Rodrigues rotation of dv about the unit     */
 /* axis n by angle alpha:  dv' = dv cos a + (n x dv) sin a + n (n.dv)(1-cos a)*/
 /* ------------------------------------------------------------------------ */
@@ -568,6 +763,13 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     } else {
       stream_d(p, &pos[3 * i], &vel[3 * i]);
     }
+  }
+
+  /* Velocities before the collision (angular-momentum correction). */
+  double* v0 = NULL;
+  if (p->angular) {
+    v0 = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    memcpy(v0, vel, sizeof(double) * 3 * (size_t)n);
   }
 
   /* Bin solvent then beads. */
@@ -706,6 +908,10 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
       for (int k = 0; k < 3; ++k)
         svel[3 * b + k] = (cb->u[3 * c + k] + dv[k]) - cb->dbar[3 * c + k];
     }
+    if (p->angular) {
+      angular_correction(p, n, pos, v0, vel, cellid, s, ncells, cb->nsol);
+      free(v0);
+    }
     return status;
   }
 
@@ -808,6 +1014,10 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
       svel[3 * b + k] = cb->u[3 * c + k] + r;
     }
   }
+  if (p->angular) {
+    angular_correction(p, n, pos, v0, vel, cellid, s, ncells, cb->nsol);
+    free(v0);
+  }
   return status;
 }
 
@@ -819,6 +1029,7 @@ static int32_t check_params(const oracle_params* p, int64_t n, int64_t nb) {
   if (p->walls_z && (p->g[2] != 0.0 || nb > 0)) return -1;
   if (p->collision != ORACLE_SRD && p->collision != ORACLE_AT) return -1;
   if (p->collision == ORACLE_AT && (p->thermostat || p->walls_z)) return -1;
+  if (p->angular && (p->walls_z || nb > 0)) return -1;
   if (nb > 0 && (p->chain_len < 1 || nb % p->chain_len != 0 || p->md_substeps < 1 ||
                  !(p->solute_mass > 0.0)))
     return -1;

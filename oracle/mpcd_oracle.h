@@ -15,6 +15,9 @@
  *   Sec. 2, Eq. (thermo) : Maxwell-Boltzmann cell thermostat, xi = sqrt(E^/Ek)
  *   Sec. 2, Eq. (at)     : Andersen-thermostat collision rule (Sec. 3.7):
  *                          v <- u + dv_i - <dv>, dv_i Gaussian per particle
+ *   Sec. 2 (after Eqs. srd and at): optional angular-momentum conservation,
+ *                          a rigid rotation of each cell's relative velocities
+ *                          that restores its angular momentum
  *   Sec. 3.6             : cylindrical-projection axis, Marsaglia-Tsang Gamma
  *                          draw with a Box-Muller normal, xi = 1 if Nc < 2
  *   Sec. 2 / Sec. 3.6    : solute beads (velocity Verlet, harmonic bonds)
@@ -70,6 +73,8 @@ typedef struct {
   double solute_mass;    /* bead mass M                                     */
   double bond_k;         /* harmonic bond constant                          */
   double bond_r0;        /* harmonic bond rest length                       */
+  int32_t angular;       /* 1 = conserve each cell's angular momentum        */
+  int32_t pad2_;
 } oracle_params;
 
 /* Philox4x32-10 (Salmon et al., SC11) on one counter block. */
@@ -111,7 +116,8 @@ void oracle_at_draw(uint64_t seed, uint64_t t, uint32_t tag, int32_t kind, doubl
  * cell id of every particle (solvent then beads) at the last step; if
  * count_out != NULL it receives the member count (solvent + beads) of every
  * cell at the last step (oracle_num_cells entries).
- * The Andersen rule takes no thermostat flag and no walls (-1 otherwise).
+ * The Andersen rule takes no thermostat flag and no walls (-1 otherwise);
+ * angular momentum conservation takes no walls and no solute (-1 otherwise).
  * Returns 0, -1 invalid argument, -4 Gamma sampler cap reached. */
 int32_t oracle_step(const oracle_params* p, int64_t n, double* pos, double* vel,
                     int64_t nb, double* spos, double* svel, uint64_t* step,
