@@ -66,7 +66,8 @@ def workload_cfg(name):
 def box_kwargs(cfg):
     kw = dict(n=cfg["n"], dt=cfg["dt"], alpha_deg=cfg["alpha_deg"], kT=cfg["kT"],
               seed=cfg["seed"], thermostat=cfg["thermostat"], precision=cfg["precision"],
-              sort_period=cfg.get("sort_period", 0), collision=cfg.get("collision", "srd"))
+              sort_period=cfg.get("sort_period", 0), collision=cfg.get("collision", "srd"),
+              angular=cfg.get("angular", False))
     if cfg.get("n_chains"):
         kw.update(chain_len=cfg["chain_len"], md_substeps=cfg["md_substeps"],
                   solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"])
@@ -161,7 +162,8 @@ def oracle_rate(cfg, budget_s, steps=None, warmup=0):
     prec = oracle.MIXED if cfg["precision"] == "mixed" else oracle.FP64
     okw = dict(n=n, dt=cfg["dt"], alpha_deg=cfg["alpha_deg"], kT=cfg["kT"], seed=cfg["seed"],
                thermostat=cfg["thermostat"], precision=prec,
-               collision=oracle.AT if cfg.get("collision") == "at" else oracle.SRD)
+               collision=oracle.AT if cfg.get("collision") == "at" else oracle.SRD,
+               angular=bool(cfg.get("angular", False)))
     if cfg.get("n_chains"):
         nch = max(1, int(round(cfg["n_chains"] * np.prod(n) / full_cells)))
         sp, sv = inputs.chains(n, nch, cfg["chain_len"], cfg["bond_r0"], kT=cfg["kT"],
@@ -326,7 +328,10 @@ def main():
     dom_ms = phases[dom]
     achieved = step_bytes * s.pos.shape[0] / (dom_ms * 1e-3) / 1e9
     # the warp-spread kernel runs mixed-model boxes without walls
-    kname = "k_cells_warp" if cfg["precision"] == "mixed" else "k_cells"
+    if cfg.get("angular"):
+        kname = "k_cells"  # one thread per cell
+    else:
+        kname = "k_cells_warp" if cfg["precision"] == "mixed" else "k_cells_warp_d"
     traffic = kernel_traffic(kname, args.workload)
     roofline = {"bound": "hbm", "kernel": f"{kname} (collide t + stream/bin t+1)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

@@ -61,7 +61,17 @@ typedef enum { MPCD_FP64 = 0, MPCD_MIXED = 1 } mpcd_precision;
  * (1/N_c) sum_j dv_j when all masses are equal; solute beads take part with
  * their mass.  It thermostats by itself, so it takes neither the thermostat
  * flag nor walls, and it needs a row capacity of at most 448 records
- * (a density below about 300 per cell). */
+ * (a density below about 300 per cell) when beads take part.
+ *
+ * Angular-momentum conservation (angular = 1; the constraint the paper cites
+ * after Eqs. srd and at, Sec. 2): after either rule every member of a cell
+ * receives omega x r_c, r_c its position relative to the cell's centre of
+ * mass and Pi omega = sum m r_c x (v - v') with the cell's inertia tensor Pi
+ * about that centre (v before, v' after the rule), so each cell keeps its
+ * angular momentum; a two-member or collinear cell takes omega = 2 dL /
+ * tr(Pi).  The mixed model sums in int64 fixed point and solves in float.
+ * Not with walls or solute (EINVAL).  These boxes run on a kernel with one
+ * thread per cell. */
 typedef enum { MPCD_SRD = 0, MPCD_AT = 1 } mpcd_collision;
 
 /* SRD parameters (Sec. 2; Sec. 4 benchmark values in brackets).  Plain
@@ -89,6 +99,8 @@ typedef struct {
   double solute_mass;    /* solute: bead mass M                              */
   double bond_k;         /* solute: harmonic bond constant k                 */
   double bond_r0;        /* solute: harmonic bond rest length r0             */
+  int32_t angular;       /* 1: conserve each cell's angular momentum (below) */
+  int32_t reserved1;
 } mpcd_params;
 
 /* Observables of the current state (Sec. 3.5, last paragraph). */

@@ -53,6 +53,8 @@ class _Params(ctypes.Structure):
         ("solute_mass", ctypes.c_double),
         ("bond_k", ctypes.c_double),
         ("bond_r0", ctypes.c_double),
+        ("angular", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
     ]
 
 
@@ -144,7 +146,7 @@ def make_params(n=(10, 10, 10), dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=
                 thermostat=False, sort_period=0, walls_z=False, body_force=(0.0, 0.0, 0.0),
                 virt_density=0.0, precision="mixed", chain_len=0, md_substeps=0,
                 solute_mass=1.0, bond_k=0.0, bond_r0=0.0, alpha=None,
-                collision="srd") -> _Params:
+                collision="srd", angular=False) -> _Params:
     p = _Params()
     p.n[:] = [int(x) for x in n]
     p.precision = MIXED if precision in ("mixed", MIXED) else FP64
@@ -165,6 +167,7 @@ def make_params(n=(10, 10, 10), dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=
     p.bond_k = float(bond_k)
     p.bond_r0 = float(bond_r0)
     p.collision = AT if collision in ("at", AT) else SRD
+    p.angular = int(bool(angular))
     return p
 
 

@@ -105,6 +105,8 @@ int validate(const mpcd_params* p, int precision_expected) {
     return fail(MPCD_EINVAL, "collision must be MPCD_SRD or MPCD_AT");
   if (p->collision == MPCD_AT && (p->thermostat || p->walls_z))
     return fail(MPCD_EINVAL, "the Andersen rule thermostats by itself: no thermostat flag, no walls");
+  if (p->angular && (p->walls_z || p->chain_len > 0))
+    return fail(MPCD_EINVAL, "angular momentum conservation takes neither walls nor solute");
   if (p->chain_len < 0 || p->chain_len > 1024) return fail(MPCD_EINVAL, "chain_len in [0, 1024]");
   if (p->chain_len > 0 && (p->md_substeps < 1 || !(p->solute_mass > 0.0)))
     return fail(MPCD_EINVAL, "solute needs md_substeps >= 1 and solute_mass > 0");
@@ -270,7 +272,8 @@ struct Engine {
   // per kernel variant: thermostat (1) | walls or beads (2) | warp-spread members (4);
   // for the warp-spread kernel bit 2 means a nonzero body force, bit 8 beads
   // and bit 16 the Andersen rule
-  static constexpr int NVAR = 32;
+  // per-cell kernel: bit 16 the Andersen rule, bit 32 the angular correction
+  static constexpr int NVAR = 64;
   int2* d_spans[NVAR] = {};
   int n_spans[NVAR] = {};
   ScanSeg* d_bsegs = nullptr;
@@ -308,11 +311,11 @@ struct Engine {
     for (int m = 0; m < 3; ++m)
       for (int v = 0; v < NVAR; ++v) {
         const bool at = (v & 16) != 0;
-        if ((v & 4) && !(at && (v & 1)))
+        if ((v & 4) && !(at && (v & 1)) && !(v & 32))
           cells_bps[m][v] =
               mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, m)
                     : cells_warpd_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, m);
-        else if (v < 4)
+        else if (!(v & 4))
           cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
         else
           cells_bps[m][v] = 1;
@@ -443,8 +446,10 @@ struct Engine {
       b->dev_index = (int)i;
       rec.push_back(b->d);
       const BoxDev& d = b->d;
-      int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0);
-      if (!d.walls && d.K <= WARP_MAX_K &&
+      const bool at = d.collision == RULE_AT;
+      int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0) | (at ? 16 : 0) |
+                    (d.angular ? 32 : 0);
+      if (!d.angular && !d.walls && d.K <= WARP_MAX_K &&
           std::max(d.n[0], std::max(d.n[1], d.n[2])) < (1 << 22)) {
         const bool force = d.g[0] != 0.0 || d.g[1] != 0.0 || d.g[2] != 0.0;
         variant = 4 | (d.thermostat ? 1 : 0) | (force ? 2 : 0) | (d.nbead > 0 ? 8 : 0) |
@@ -664,10 +669,11 @@ struct Engine {
     d.thermostat = p.thermostat ? 1 : 0;
     d.collision = p.collision;
     d.K = row_capacity(p, nsol);
-    if (d.collision == RULE_AT &&
+    d.angular = p.angular ? 1 : 0;
+    if (d.collision == RULE_AT && nbead > 0 &&
         (d.K > WARP_MAX_K || std::max(p.n[0], std::max(p.n[1], p.n[2])) >= (1 << 22)))
-      return fail(MPCD_EINVAL, "the Andersen rule needs a row capacity <= 448 (density below "
-                               "about 300) and fewer than 2^22 cells per axis");
+      return fail(MPCD_EINVAL, "the Andersen rule with solute needs a row capacity <= 448 "
+                               "(density below about 300) and fewer than 2^22 cells per axis");
     d.ovf_cap = (int32_t)std::max<int64_t>(nsol, 1);
     d.tc = BEAD_TILE;
     d.nctiles = (int32_t)((C + BEAD_TILE - 1) / BEAD_TILE);

@@ -14,6 +14,13 @@
 // set), mode C only collides, in place (to complete a step before the state is
 // read).  Nothing else touches the particles: no separate sort, scan or
 // reorder pass exists, and every record moves as one 32-byte sector.
+//
+// This kernel also carries the Andersen rule (Eq. at, Sec. 3.7) for rows too
+// long for the warp-spread kernel, and the angular-momentum-conserving form
+// of either rule (Sec. 2: the constraint the paper cites after Eqs. srd and
+// at): a second pass over the cell's members forms dL = sum m r_c x (v - v')
+// and the inertia tensor about the cell's centre of mass, and every member
+// then receives omega x r_c with Pi omega = dL.
 #include "dev_collide.cuh"
 #include "dev_rows.cuh"
 #include "dev_stream.cuh"
@@ -22,7 +29,56 @@
 
 namespace mpcd {
 
-template <bool MIXED, bool THERMO, bool EXTRA, int MODE>
+namespace {
+
+// Coordinate of x relative to the shifted cell whose index along the axis is
+// i (in [0, 1); a member wrapped across the box edge is brought back).
+__device__ __forceinline__ double rel_pos(double x, double s, int i, double L) {
+  double d = (x - s) - (double)i;
+  if (d < 0.0) d += L;
+  else if (d >= 1.0) d -= L;
+  return d;
+}
+
+// Per-cell sums of the angular correction: positions (centre of mass), then
+// r_c x (v - v') and the inertia tensor entries (|r_c|^2 - r_c r_c^T: xx, xy,
+// xz, yy, yz, zz with the off-diagonal products summed positive).  Mixed
+// model: int64 sums of rne(term 2^32) of float terms; FP64: double sums.
+template <bool MIXED> struct AngAcc;
+template <> struct AngAcc<true> {
+  long long q[3] = {0, 0, 0}, l[3] = {0, 0, 0}, p[6] = {0, 0, 0, 0, 0, 0};
+};
+template <> struct AngAcc<false> {
+  double q[3] = {0, 0, 0}, l[3] = {0, 0, 0}, p[6] = {0, 0, 0, 0, 0, 0};
+};
+
+// omega from Pi omega = dL, Pi = [[a, b, c], [b, d, e], [c, e, f]]: by the
+// adjugate when Pi is well conditioned (nc >= 3), else 2 dL / tr(Pi), the
+// solution on the plane normal to a two-member (or collinear) cell.
+template <typename T>
+__device__ __forceinline__ void solve_omega(int nc, const T P[6], const T dL[3], T w[3]) {
+  const T a = P[0], b = P[1], c = P[2], d = P[3], e = P[4], f = P[5];
+  const T A = d * f - e * e, Bc = c * e - b * f, C = b * e - c * d;
+  const T D = a * f - c * c, E = b * c - a * e, F = a * d - b * b;
+  const T det = a * A + b * Bc + c * C;
+  const T tr = a + d + f;
+  const T t3 = tr / (T)3;
+  if (nc >= 3 && det > (T)1e-6 * (t3 * t3 * t3)) {
+    w[0] = (A * dL[0] + Bc * dL[1] + C * dL[2]) / det;
+    w[1] = (Bc * dL[0] + D * dL[1] + E * dL[2]) / det;
+    w[2] = (C * dL[0] + E * dL[1] + F * dL[2]) / det;
+  } else if (tr > (T)0) {
+    const T g = (T)2 / tr;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w[k] = dL[k] * g;
+  } else {
+    w[0] = w[1] = w[2] = (T)0;
+  }
+}
+
+}  // namespace
+
+template <bool MIXED, bool THERMO, bool EXTRA, int MODE, bool AT, bool ANG>
 __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxes,
                                                  const int2* __restrict__ spans, int nspans,
                                                  int* err) {
@@ -30,6 +86,7 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
   using R = rec_t<MIXED>;
   __shared__ long long sSn[3];  // shift of the step the records are binned for
   __shared__ long long sSz;     // z shift of the collision step (wall-cut cells)
+  __shared__ long long sSc[3];  // shift of the collision step (angular correction)
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
     const int2 tt = spans[sp];
     const BoxDev& B = boxes[tt.x];
@@ -42,6 +99,7 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
         shift_units(B, t, S);
         sSz = S[2];
       }
+      if (ANG && MODE != MODE_P) shift_units(B, t, sSc);
     }
     __syncthreads();
     const int cell = tt.y + (int)threadIdx.x;
@@ -74,23 +132,74 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
       }
     if (!any) continue;
 
-    CellParams<T> prm;
+    CellParams<T> prm;  // the Andersen rule keeps the mean random velocity in prm.n
+    T om[3] = {(T)0, (T)0, (T)0}, rcm[3] = {(T)0, (T)0, (T)0};
+    int ic[3] = {0, 0, 0};
+    double sc[3] = {0.0, 0.0, 0.0};
+    if (ANG && MODE != MODE_P) {
+      ic[0] = cell % B.n[0];
+      ic[1] = (cell / B.n[0]) % B.n[1];
+      ic[2] = cell / (B.n[0] * B.n[1]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sc[k] = (double)sSc[k] * 0x1p-32;
+    }
+    // position of a member relative to its cell, in the model's type
+    auto rel = [&](const T r[3], T o[3]) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o[k] = (T)rel_pos((double)r[k], sc[k], ic[k], B.L[k]);
+    };
+    // Eq. at: random velocity of a member
+    auto draw_dv = [&](uint32_t tag, T dv[3]) {
+      if constexpr (MIXED) at_draw(B, t, tag, 0u, B.sig_f, dv);
+      else at_draw(B, t, tag, 0u, B.sig, dv);
+    };
+    // the collision rule without the angular correction
+    auto base_rule = [&](T w[3], uint32_t tag) {
+      if (AT) {
+        T dv[3];
+        draw_dv(tag, dv);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) w[k] = (prm.u[k] + dv[k]) - prm.n[k];
+      } else {
+        collide_one<MIXED>(B, prm, w, THERMO);
+      }
+    };
     if (MODE != MODE_P) {
       // ---- cell properties (Sec. 3.5) ----
       CellAcc<MIXED> a;
+      CellAcc<MIXED> ad;  // Andersen rule: sums of the random velocities
+      AngAcc<MIXED> g;
+      auto add_member = [&](const R* p) {
+        if (AT || ANG) {
+          T r[3], w[3];
+          uint32_t tag;
+          load_rec(p, r, w, tag);
+          a.add_solvent(B, w);
+          if (AT) {
+            T dv[3];
+            draw_dv(tag, dv);
+            ad.add_solvent(B, dv);
+          }
+          if (ANG) {
+            T x[3];
+            rel(r, x);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              if constexpr (MIXED) g.q[k] += fix32_rne(x[k]);
+              else g.q[k] += x[k];
+            }
+          }
+        } else {
+          T w[3];
+          load_v(p, w);
+          a.add_solvent(B, w);
+        }
+      };
 #pragma unroll 4
-      for (int k = 0; k < nrow; ++k) {
-        T w[3];
-        load_v(row + k, w);
-        a.add_solvent(B, w);
-      }
+      for (int k = 0; k < nrow; ++k) add_member(row + k);
       if (has_ovf)
         for (uint32_t j = 0; j < novf; ++j)
-          if (ovf_cell[j] == (uint32_t)cell) {
-            T w[3];
-            load_v(ovf + j, w);
-            a.add_solvent(B, w);
-          }
+          if (ovf_cell[j] == (uint32_t)cell) add_member(ovf + j);
       auto solvent_energy = [&](const T u[3], CellAcc<MIXED>& acc) {
 #pragma unroll 4
         for (int k = 0; k < nrow; ++k) {
@@ -109,9 +218,78 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
       const double sz = EXTRA ? (double)sSz * 0x1p-32 : 0.0;
       T u[3];
       cell_mean<MIXED>(B, t, (uint32_t)cell, sz, a, EXTRA ? nbt : 0, bead_in, EXTRA, u);
-      if (THERMO) solvent_energy(u, a);
-      cell_finish<MIXED>(B, t, (uint32_t)cell, a, u, EXTRA ? nbt : 0, bead_in, THERMO, EXTRA, prm,
-                         err);
+      if (AT) {  // Eq. at: u and dbar = sum m dv / sum m
+        T dbar[3];
+        ad.mean_velocity(B, dbar, false);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          prm.u[k] = u[k];
+          prm.n[k] = dbar[k];
+        }
+        prm.xi = (T)1;
+      } else {
+        if (THERMO) solvent_energy(u, a);
+        cell_finish<MIXED>(B, t, (uint32_t)cell, a, u, EXTRA ? nbt : 0, bead_in, THERMO, EXTRA, prm,
+                           err);
+      }
+      if (ANG) {
+        // centre of mass in the cell frame, then dL = sum m r_c x (v - v')
+        // and the inertia tensor about it
+        const int ns = a.ns;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (MIXED) rcm[k] = (i64_to_float(g.q[k]) * 0x1p-32f) / small_to_float(ns);
+          else rcm[k] = g.q[k] / (double)ns;
+        }
+        auto add_moment = [&](const R* p) {
+          T r[3], w[3];
+          uint32_t tag;
+          load_rec(p, r, w, tag);
+          T x[3], rc[3], v2[3] = {w[0], w[1], w[2]};
+          rel(r, x);
+          base_rule(v2, tag);
+          T d[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            rc[k] = x[k] - rcm[k];
+            d[k] = w[k] - v2[k];
+          }
+          const T cx[3] = {rc[1] * d[2] - rc[2] * d[1], rc[2] * d[0] - rc[0] * d[2],
+                           rc[0] * d[1] - rc[1] * d[0]};
+          const T te[6] = {rc[1] * rc[1] + rc[2] * rc[2], rc[0] * rc[1], rc[0] * rc[2],
+                           rc[0] * rc[0] + rc[2] * rc[2], rc[1] * rc[2],
+                           rc[0] * rc[0] + rc[1] * rc[1]};
+          if constexpr (MIXED) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) g.l[k] += fix32_rne(cx[k]);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) g.p[k] += fix32_rne(te[k]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) g.l[k] += B.m * cx[k];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) g.p[k] += B.m * te[k];
+          }
+        };
+        for (int k = 0; k < nrow; ++k) add_moment(row + k);
+        if (has_ovf)
+          for (uint32_t j = 0; j < novf; ++j)
+            if (ovf_cell[j] == (uint32_t)cell) add_moment(ovf + j);
+        T P[6], dL[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (MIXED) dL[k] = B.m_f * (i64_to_float(g.l[k]) * 0x1p-32f);
+          else dL[k] = g.l[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          T e;
+          if constexpr (MIXED) e = B.m_f * (i64_to_float(g.p[k]) * 0x1p-32f);
+          else e = g.p[k];
+          P[k] = (k == 1 || k == 2 || k == 4) ? -e : e;
+        }
+        solve_omega<T>(ns, P, dL, om);
+      }
     }
 
     // ---- members: collide, then stream and bin for the next step ----
@@ -119,7 +297,19 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
       T r[3], w[3];
       uint32_t tag;
       load_rec(p, r, w, tag);
-      if (MODE != MODE_P) collide_one<MIXED>(B, prm, w, THERMO);
+      if (MODE != MODE_P) {
+        if (AT || ANG) base_rule(w, tag);
+        else collide_one<MIXED>(B, prm, w, THERMO);
+        if (ANG) {  // v'' = v' + omega x r_c
+          T x[3], rc[3];
+          rel(r, x);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) rc[k] = x[k] - rcm[k];
+          w[0] = w[0] + (om[1] * rc[2] - om[2] * rc[1]);
+          w[1] = w[1] + (om[2] * rc[0] - om[0] * rc[2]);
+          w[2] = w[2] + (om[0] * rc[1] - om[1] * rc[0]);
+        }
+      }
       if (MODE == MODE_C) {
         store_rec(p, r, w, tag);
         return;
@@ -217,20 +407,31 @@ __global__ void k_extract(const BoxDev* __restrict__ box, real_t<MIXED>* __restr
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-template <bool M, bool TH, bool EX, int MODE>
+template <bool M, bool TH, bool EX, int MODE, bool AT, bool ANG>
 static void* cells_fn() {
-  return (void*)k_cells<M, TH, EX, MODE>;
+  return (void*)k_cells<M, TH, EX, MODE, AT, ANG>;
+}
+
+// variant bits: 1 thermostat, 2 walls or beads, 16 Andersen rule, 32 angular
+// correction (the last two without walls or beads; the Andersen rule without
+// the thermostat).
+template <bool M, int MODE>
+static void* cells_variant_m(int variant) {
+  const bool th = (variant & 1) != 0, ex = (variant & 2) != 0;
+  const bool at = (variant & 16) != 0, ang = (variant & 32) != 0;
+  if (at) return ang ? cells_fn<M, false, false, MODE, true, true>()
+                     : cells_fn<M, false, false, MODE, true, false>();
+  if (ang) return th ? cells_fn<M, true, false, MODE, false, true>()
+                     : cells_fn<M, false, false, MODE, false, true>();
+  if (th) return ex ? cells_fn<M, true, true, MODE, false, false>()
+                    : cells_fn<M, true, false, MODE, false, false>();
+  return ex ? cells_fn<M, false, true, MODE, false, false>()
+            : cells_fn<M, false, false, MODE, false, false>();
 }
 
 template <int MODE>
 static void* cells_variant_mode(bool mixed, int variant) {
-  const bool th = (variant & 1) != 0, ex = (variant & 2) != 0;
-  if (mixed) {
-    if (th) return ex ? cells_fn<true, true, true, MODE>() : cells_fn<true, true, false, MODE>();
-    return ex ? cells_fn<true, false, true, MODE>() : cells_fn<true, false, false, MODE>();
-  }
-  if (th) return ex ? cells_fn<false, true, true, MODE>() : cells_fn<false, true, false, MODE>();
-  return ex ? cells_fn<false, false, true, MODE>() : cells_fn<false, false, false, MODE>();
+  return mixed ? cells_variant_m<true, MODE>(variant) : cells_variant_m<false, MODE>(variant);
 }
 
 static void* cells_variant(bool mixed, int variant, int mode) {

@@ -9,7 +9,9 @@ namespace mpcd {
 
 // ---- fused step on cell rows (k_cells.cu) ----
 // mode: MODE_P stream + bin, MODE_F collide + stream + bin, MODE_C collide in place.
-// variant = (thermostat ? 1 : 0) | (solute beads or walls ? 2 : 0).
+// variant = (thermostat ? 1 : 0) | (solute beads or walls ? 2 : 0) |
+// (Andersen rule ? 16 : 0) | (angular-momentum correction ? 32 : 0); the last
+// two without solute or walls.
 int cells_blocks_per_sm(bool mixed, int variant, int mode);
 void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const int2* spans,
                   int nspans, int grid, int* err, cudaStream_t s);
@@ -17,8 +19,7 @@ void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const 
 // lanes of a warp (k_cells_warp.cu); valid for row capacities up to
 // WARP_MAX_K and boxes below 2^22 cells per axis.  force: nonzero body force;
 // beads: the box has solute beads; at: Andersen-thermostat rule (Eq. at)
-// instead of the rotation (thermo is then false).  The Andersen rule runs
-// only on these kernels.
+// instead of the rotation (thermo is then false).
 constexpr int WARP_MAX_K = 448;
 int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode);
 void launch_cells_warp(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,

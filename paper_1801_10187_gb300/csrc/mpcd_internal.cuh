@@ -109,6 +109,8 @@ struct BoxDev {
   // component, solvent and beads
   double sig, sigb;
   float sig_f, sigb_f;
+  int32_t angular;      // 1: angular-momentum correction after the collision rule
+  int32_t pad_a;
 };
 
 // Segments for the segmented exclusive scan (cells of each box, and bead

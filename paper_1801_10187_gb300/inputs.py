@@ -108,6 +108,10 @@ WORKLOADS = {
     "srd-100c-rho10-mixed-at": dict(n=(100, 100, 100), density=10, alpha_deg=130.0, dt=0.1,
                                     kT=1.0, seed=2, thermostat=False, precision="mixed",
                                     steps=2000, collision="at"),
+    # the benchmark fluid with angular-momentum conservation
+    "srd-100c-rho10-mixed-angular": dict(n=(100, 100, 100), density=10, alpha_deg=130.0,
+                                         dt=0.1, kT=1.0, seed=2, thermostat=False,
+                                         precision="mixed", steps=2000, angular=True),
     # the benchmark fluid at 8 * 10^7 particles (a 50M+ particle box)
     "srd-200c-rho10-mixed": dict(n=(200, 200, 200), density=10, alpha_deg=130.0, dt=0.1,
                                  kT=1.0, seed=4, thermostat=False, precision="mixed",

@@ -158,12 +158,24 @@ def test_at_invalid_combinations_raise():
         pkg.Box(n=(4, 4, 4), collision="at", thermostat=True)
     with pytest.raises(pkg.MpcdError):
         pkg.Box(n=(4, 4, 4), collision="at", walls_z=True)
-    box = pkg.Box(n=(2, 2, 2), collision="at")
-    s = inputs.solvent((2, 2, 2), 400, seed=1, mixed=True)  # rows above 448 records
+    # solute with rows above 448 records (density 400)
+    kw = dict(chain_len=4, md_substeps=1, solute_mass=5.0, bond_k=10.0, bond_r0=0.5)
+    box = pkg.Box(n=(2, 2, 2), collision="at", **kw)
+    s = inputs.solvent((2, 2, 2), 400, seed=1, mixed=True)
+    sp, sv = inputs.chains((2, 2, 2), 1, 4, 0.5, seed=2)
     with pytest.raises(pkg.MpcdError) as e:
-        box.set_state(s.pos, s.vel)
+        box.set_state(s.pos, s.vel, sp, sv)
     assert e.value.code == pkg.MPCD_EINVAL
     box.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_at_dense_rows_per_cell_kernel(precision):
+    # density 400: rows of 524 records, beyond the warp-spread kernel; the
+    # Andersen rule runs on the per-cell kernel, same results
+    s = inputs.solvent((3, 3, 2), 400, seed=8, mixed=precision == "mixed")
+    got, want = run_at((3, 3, 2), s.pos, s.vel, precision, 3, 8)
+    check(got, want, precision, steps=3)
 
 
 def test_at_thermalises_and_conserves_momentum():

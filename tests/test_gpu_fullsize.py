@@ -41,7 +41,7 @@ def rel_err(v, ref, kT=1.0, m=1.0):
 def box_kw(cfg):
     kw = dict(n=cfg["n"], dt=cfg["dt"], alpha_deg=cfg["alpha_deg"], kT=cfg["kT"],
               seed=cfg["seed"], thermostat=cfg["thermostat"], precision=cfg["precision"],
-              collision=cfg.get("collision", "srd"))
+              collision=cfg.get("collision", "srd"), angular=cfg.get("angular", False))
     if cfg.get("n_chains"):
         kw.update(chain_len=cfg["chain_len"], md_substeps=cfg["md_substeps"],
                   solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"])
@@ -56,7 +56,7 @@ def oracle_params(kw):
         collision=oracle.AT if kw["collision"] == "at" else oracle.SRD,
         chain_len=kw.get("chain_len", 0), md_substeps=kw.get("md_substeps", 0),
         solute_mass=kw.get("solute_mass", 1.0), bond_k=kw.get("bond_k", 0.0),
-        bond_r0=kw.get("bond_r0", 0.0))
+        bond_r0=kw.get("bond_r0", 0.0), angular=kw["angular"])
 
 
 def run_full(name, steps=2):
@@ -92,7 +92,7 @@ def run_full(name, steps=2):
 
 
 @pytest.mark.parametrize("name", ["srd-100c-rho10-mixed", "srd-100c-rho10-fp64",
-                                  "srd-100c-rho10-mixed-at"])
+                                  "srd-100c-rho10-mixed-at", "srd-100c-rho10-mixed-angular"])
 def test_fullsize_10m(name):
     run_full(name)
 
