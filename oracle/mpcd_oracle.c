@@ -522,6 +522,19 @@ static double rel_pos(const oracle_params* p, double x, double s, int64_t i, int
   return d;
 }
 
+/* The mixed model's relative position, in float: x = fl + f with fl = floor(x)
+ * and f exact, i0 = floor(x - s) the unwrapped cell coordinate of the
+ * binning (exact), and x - s - i0 = (f - s) + (fl - i0), with s rounded to
+ * float and fl - i0 in {-1, 0, 1}. */
+static float rel_pos_f(double x, double s) {
+  float xf = (float)x;
+  float fl = floorf(xf);
+  float f = xf - fl;
+  double i0 = floor((double)xf - s);
+  float adj = (float)((double)fl - i0);
+  return (f - (float)s) + adj;
+}
+
 static void cell_coords(const oracle_params* p, int32_t c, int64_t ic[3]) {
   int64_t nx = p->n[0], ny = p->n[1];
   ic[0] = c % nx;
@@ -589,7 +602,8 @@ static void angular_correction(const oracle_params* p, int64_t n, const double* 
       int64_t ic_[3];                                                     \
       cell_coords(p, cellid[i], ic_);                                     \
       for (int k_ = 0; k_ < 3; ++k_)                                      \
-        r[k_] = rel_pos(p, pos[3 * (i) + k_], s[k_], ic_[k_], k_);        \
+        r[k_] = mixed ? (double)rel_pos_f(pos[3 * (i) + k_], s[k_])       \
+                      : rel_pos(p, pos[3 * (i) + k_], s[k_], ic_[k_], k_); \
     } while (0)
   /* centre of mass of each cell */
   for (int64_t i = 0; i < n; ++i) {

@@ -40,6 +40,29 @@ __device__ __forceinline__ double rel_pos(double x, double s, int i, double L) {
   return d;
 }
 
+// The mixed model's coordinate relative to the shifted cell, in float: with
+// x = fl + f (fl = floor(x) by a round-down add of 2^23, f exact) and the
+// unwrapped cell coordinate i0 = fl - [f < lo] + [f >= hi] of the exact
+// binning (lo, hi: the float thresholds of the shift s), x - s - i0 =
+// (f - sf) + ([f < lo] - [f >= hi]) with sf = RN(s).  Needs 0 <= x < 2^23.
+__device__ __forceinline__ float rel_pos_f(float x, float sf, float lo, float hi) {
+  const float fl = __fsub_rn(__fadd_rd(x, 8388608.0f), 8388608.0f);
+  const float f = __fsub_rn(x, fl);
+  const float adj = (f < lo ? 1.0f : 0.0f) - (f >= hi ? 1.0f : 0.0f);
+  return (f - sf) + adj;
+}
+
+// Float thresholds of the shift s = S 2^-32: f < s iff f < lo, f >= 1 + s
+// iff f >= hi, for every float f in [0, 1).
+__device__ __forceinline__ void shift_thresholds(long long S, float& sf, float& lo, float& hi) {
+  const double s = (double)S * 0x1p-32;
+  sf = (float)s;
+  lo = ((double)sf < s) ? nextafterf(sf, INFINITY) : sf;
+  const double t = 1.0 + s;
+  const float th = (float)t;
+  hi = ((double)th < t) ? nextafterf(th, INFINITY) : th;
+}
+
 // Per-cell sums of the angular correction: positions (centre of mass), then
 // r_c x (v - v') and the inertia tensor entries (|r_c|^2 - r_c r_c^T: xx, xy,
 // xz, yy, yz, zz with the off-diagonal products summed positive).  Mixed
@@ -87,6 +110,7 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
   __shared__ long long sSn[3];  // shift of the step the records are binned for
   __shared__ long long sSz;     // z shift of the collision step (wall-cut cells)
   __shared__ long long sSc[3];  // shift of the collision step (angular correction)
+  __shared__ float sCf[3][3];   // its float form and thresholds (mixed model)
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
     const int2 tt = spans[sp];
     const BoxDev& B = boxes[tt.x];
@@ -99,7 +123,10 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
         shift_units(B, t, S);
         sSz = S[2];
       }
-      if (ANG && MODE != MODE_P) shift_units(B, t, sSc);
+      if (ANG && MODE != MODE_P) {
+        shift_units(B, t, sSc);
+        for (int k = 0; k < 3; ++k) shift_thresholds(sSc[k], sCf[0][k], sCf[1][k], sCf[2][k]);
+      }
     }
     __syncthreads();
     const int cell = tt.y + (int)threadIdx.x;
@@ -146,7 +173,10 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
     // position of a member relative to its cell, in the model's type
     auto rel = [&](const T r[3], T o[3]) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) o[k] = (T)rel_pos((double)r[k], sc[k], ic[k], B.L[k]);
+      for (int k = 0; k < 3; ++k) {
+        if constexpr (MIXED) o[k] = rel_pos_f(r[k], sCf[0][k], sCf[1][k], sCf[2][k]);
+        else o[k] = rel_pos(r[k], sc[k], ic[k], B.L[k]);
+      }
     };
     // Eq. at: random velocity of a member
     auto draw_dv = [&](uint32_t tag, T dv[3]) {
