@@ -53,14 +53,34 @@ constexpr int STAGE = 256;        // member velocities staged per block of pass 
 constexpr int STAGE_PAD = STAGE + STAGE / 32;
 constexpr int CHUNK = 3;          // windows of 32 members per chunk of pass 2
 
-// 16-byte asynchronous copy global -> shared (bypassing L1), and the wait for
-// all of this thread's outstanding copies.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
+// The wait for all of this thread's outstanding asynchronous copies (16-byte
+// global -> shared copies that bypass L1, issued below with an L2 policy).
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// L2 policy "evict first": pass 2 reads each record for the last time in the
+// step and the records it writes are read again only next step, so neither
+// should push out records that pass 1 has read and pass 2 has yet to re-read.
+// (At 10^7 particles: DRAM traffic 761 -> 678 MB per step.)
+__device__ __forceinline__ unsigned long long l2_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void cp_async16_last_use(void* smem, const void* gmem,
+                                                    unsigned long long pol) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem),
+               "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void store_rec_streaming(RecF* p, const float r[3], const float v[3],
+                                                    uint32_t tag, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8}, %9;" ::"l"(p),
+               "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(__uint_as_float(tag)), "f"(r[0]), "f"(r[1]),
+               "f"(r[2]), "f"(0.0f), "l"(pol)
+               : "memory");
 }
 
 struct WarpShared {
@@ -676,7 +696,7 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
     // the overflow list beyond the row capacity)
     auto emit = [&](const float r[3], const float w[3], uint32_t tag, uint32_t c2, uint32_t slot) {
       if (slot < (uint32_t)H.K) {
-        store_rec(H.rows_out + (size_t)c2 * H.K + slot, r, w, tag);
+        store_rec_streaming(H.rows_out + (size_t)c2 * H.K + slot, r, w, tag, l2_evict_first());
       } else {
         const uint32_t j = atomicAdd(H.ovf_n_out, 1u);
         if (j < (uint32_t)H.ovf_cap) {
@@ -699,8 +719,9 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
         const int m = base + (w << 5) + lane;
         if (m < N) {
           const R* p = member(m, owner_of(m));
-          cp_async16(&W.buf[w][0][lane], p);
-          cp_async16(&W.buf[w][1][lane], reinterpret_cast<const float4*>(p) + 1);
+          const unsigned long long pol = l2_evict_first();
+          cp_async16_last_use(&W.buf[w][0][lane], p, pol);
+          cp_async16_last_use(&W.buf[w][1][lane], reinterpret_cast<const float4*>(p) + 1, pol);
         }
       }
       cp_async_wait_all();  // each lane reads back only its own copies
