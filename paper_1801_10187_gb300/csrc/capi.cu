@@ -310,10 +310,14 @@ struct Engine {
     }
     for (int m = 0; m < 3; ++m)
       for (int v = 0; v < NVAR; ++v) {
-        const bool at = (v & 16) != 0;
-        if ((v & 4) && !(at && (v & 1)) && !(v & 32))
+        const bool at = (v & 16) != 0, ang = (v & 32) != 0;
+        if ((v & 4) && ang)  // warp-spread angular correction: mixed SRD, no thermostat or beads
+          cells_bps[m][v] = (mixed && !(v & (1 | 8 | 16)))
+                                ? cells_warp_blocks_per_sm(false, (v & 2) != 0, false, false, true, m)
+                                : 1;
+        else if ((v & 4) && !(at && (v & 1)))
           cells_bps[m][v] =
-              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, m)
+              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, false, m)
                     : cells_warpd_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, m);
         else if (!(v & 4))
           cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
@@ -449,11 +453,12 @@ struct Engine {
       const bool at = d.collision == RULE_AT;
       int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0) | (at ? 16 : 0) |
                     (d.angular ? 32 : 0);
-      if (!d.angular && !d.walls && d.K <= WARP_MAX_K &&
+      const bool warp_ang = mixed && !d.thermostat && !at && d.nbead == 0;
+      if ((!d.angular || warp_ang) && !d.walls && d.K <= WARP_MAX_K &&
           std::max(d.n[0], std::max(d.n[1], d.n[2])) < (1 << 22)) {
         const bool force = d.g[0] != 0.0 || d.g[1] != 0.0 || d.g[2] != 0.0;
         variant = 4 | (d.thermostat ? 1 : 0) | (force ? 2 : 0) | (d.nbead > 0 ? 8 : 0) |
-                  (d.collision == RULE_AT ? 16 : 0);
+                  (d.collision == RULE_AT ? 16 : 0) | (d.angular ? 32 : 0);
       }
       for (int c0 = 0; c0 < d.ncells; c0 += BLOCK) sp[variant].push_back(make_int2((int)i, c0));
       if (d.nbead > 0) {
@@ -502,8 +507,8 @@ struct Engine {
       const int grid = grid_for(n_spans[v], cells_bps[mode][v]);
       const bool at = (v & 16) != 0;
       if ((v & 4) && mixed)
-        launch_cells_warp((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, mode, d_boxes,
-                          d_spans[v], n_spans[v], grid, d_err, stream);
+        launch_cells_warp((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, (v & 32) != 0, mode,
+                          d_boxes, d_spans[v], n_spans[v], grid, d_err, stream);
       else if (v & 4)
         launch_cells_warpd((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, mode, d_boxes,
                            d_spans[v], n_spans[v], grid, d_err, stream);

@@ -35,6 +35,7 @@
 // pass 1 also sums each member's Gaussian random velocity dv (drawn from its
 // tag) in the same exact split form, the cell phase forms the mass-weighted
 // mean dv of the cell, and pass 2 draws dv again and sets v = (u + dv) - dbar.
+#include "dev_angular.cuh"
 #include "dev_collide.cuh"
 #include "dev_rows.cuh"
 #include "dev_stream.cuh"
@@ -151,9 +152,28 @@ constexpr size_t SPAN_SMEM = (sizeof(SpanParams) + 15) & ~(size_t)15;
 constexpr size_t BLOCK_SMEM = SPAN_SMEM + WARPS * WARP_SMEM;
 constexpr size_t BLOCK_SMEM_BEADS = BLOCK_SMEM + WARPS * sizeof(BeadShared);
 
-__host__ __device__ constexpr size_t block_smem(bool beads, bool at) {
+// Angular-momentum correction (SRD without thermostat or beads): the float
+// frame of the collision step's shift (per block), and per warp the staged
+// relative positions of the members, split sums per cell of the positions,
+// of r_c x (v - v') and of the six inertia-tensor entries, and per cell the
+// centre of mass and omega.
+struct AngBlock {
+  float sf[3], lo[3], hi[3];
+  int pad_[3];
+};
+struct AngWarp {
+  float sr[3][STAGE_PAD];
+  int qh[3][32], ql[3][32];
+  int lh[3][32], ll[3][32];
+  int ph[6][32], pl[6][32];
+  float4 rc[32];  // (centre of mass in the cell frame, 0)
+  float4 om[32];  // (omega, 0)
+};
+
+__host__ __device__ constexpr size_t block_smem(bool beads, bool at, bool ang = false) {
   return BLOCK_SMEM + (beads ? WARPS * sizeof(BeadShared) : 0) +
-         (at ? WARPS * (beads ? sizeof(ATShared<DV_CAP_BEADS>) : sizeof(ATShared<DV_CAP>)) : 0);
+         (at ? WARPS * (beads ? sizeof(ATShared<DV_CAP_BEADS>) : sizeof(ATShared<DV_CAP>)) : 0) +
+         (ang ? sizeof(AngBlock) + WARPS * sizeof(AngWarp) : 0);
 }
 
 // floor(x - s) for 0 <= x < 2^22 and s = S 2^-32 in [-1/2, 1/2), exactly:
@@ -193,8 +213,10 @@ __device__ __forceinline__ float wrap_fast(float x, float L) {
 // AT selects the Andersen rule (then THERMO is false): its two Box-Muller
 // draws per member want registers for independent chains, and its cache of
 // random velocities wants shared memory, so it runs two blocks per SM.
-template <bool THERMO, int MODE, bool FORCE, bool BEADS, bool AT>
-__global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k_cells_warp(const BoxDev* __restrict__ boxes,
+// ANG adds the angular-momentum correction to SRD (then THERMO, BEADS and AT
+// are false); its shared memory allows two blocks per SM.
+template <bool THERMO, int MODE, bool FORCE, bool BEADS, bool AT, bool ANG>
+__global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 3 : 4)) k_cells_warp(const BoxDev* __restrict__ boxes,
                                                          const int2* __restrict__ spans,
                                                          int nspans, int* err) {
   using R = RecF;
@@ -206,6 +228,8 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
   BeadShared& BS = reinterpret_cast<BeadShared*>(smem_ + BLOCK_SMEM)[threadIdx.x >> 5];
   constexpr int DVC = BEADS ? DV_CAP_BEADS : DV_CAP;
   ATShared<DVC>& AS = reinterpret_cast<ATShared<DVC>*>(smem_ + block_smem(BEADS, false))[threadIdx.x >> 5];
+  AngBlock& AB = *reinterpret_cast<AngBlock*>(smem_ + block_smem(BEADS, AT));
+  AngWarp& AG = reinterpret_cast<AngWarp*>(smem_ + block_smem(BEADS, AT) + sizeof(AngBlock))[threadIdx.x >> 5];
   const SpanParams& H = sp_;
   int box_of_params = -1;  // the span parameters depend on the box only
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
@@ -233,6 +257,11 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
           long long S[3];
           shift_units(B, MODE == MODE_P ? t : t + 1ull, S);
           for (int q = 0; q < 3; ++q) bin_thresholds(S[q], P.lo[q], P.hi[q]);
+        }
+        if (ANG && MODE != MODE_P) {  // frame of the collision step's cells
+          long long S[3];
+          shift_units(B, t, S);
+          for (int q = 0; q < 3; ++q) shift_thresholds(S[q], AB.sf[q], AB.lo[q], AB.hi[q]);
         }
       }
       __syncthreads();
@@ -302,6 +331,24 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
             if (AT) AS.tag[js] = __float_as_uint(a[u].w);
           }
         }
+        if (ANG && MODE != MODE_P) {  // positions relative to the collision cell
+          float4 b[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j0 + (u << 5) + lane;
+            if (j < cnt) b[u] = reinterpret_cast<const float4*>(member(sbase + j, owner_of(sbase + j)))[1];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = j0 + (u << 5) + lane;
+            if (j < cnt) {
+              const int js = j + (j >> 5);
+              AG.sr[0][js] = rel_pos_f(b[u].x, AB.sf[0], AB.lo[0], AB.hi[0]);
+              AG.sr[1][js] = rel_pos_f(b[u].y, AB.sf[1], AB.lo[1], AB.hi[1]);
+              AG.sr[2][js] = rel_pos_f(b[u].z, AB.sf[2], AB.lo[2], AB.hi[2]);
+            }
+          }
+        }
         if (AT && MODE != MODE_P) {  // Eq. at: random velocities of the cached members
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
@@ -348,6 +395,10 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
           AS.h[q][lane] = 0;
           AS.l[q][lane] = 0;
         }
+        if (ANG) {
+          AG.qh[q][lane] = 0;
+          AG.ql[q][lane] = 0;
+        }
       }
       __syncwarp();
       bool slow = false, slow_d = false;
@@ -356,7 +407,17 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
         stage(sbase, cnt);
         int Hs[3] = {0, 0, 0}, Ls[3] = {0, 0, 0};
         int Hd[3] = {0, 0, 0}, Ld[3] = {0, 0, 0};
+        int Hq[3] = {0, 0, 0}, Lq[3] = {0, 0, 0};
         share(sbase, cnt, [&](int o, int js, bool last) {
+          if (ANG) {  // |position in the cell frame| < 2: the split never fails
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              int h, l;
+              split32(AG.sr[q][js], h, l);
+              Hq[q] += h;
+              Lq[q] += l;
+            }
+          }
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             int h, l;
@@ -402,6 +463,12 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
                 atomicAdd(&AS.l[q][o], Ld[q]);
                 Hd[q] = 0;
                 Ld[q] = 0;
+              }
+              if (ANG) {
+                atomicAdd(&AG.qh[q][o], Hq[q]);
+                atomicAdd(&AG.ql[q][o], Lq[q]);
+                Hq[q] = 0;
+                Lq[q] = 0;
               }
             }
           }
@@ -628,6 +695,145 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
         });
       }
       __syncwarp();
+      if (ANG) {
+        // ---- angular-momentum correction: centre of mass, then pass 1b ----
+        auto rel_of = [&](const R* p, float x[3]) {
+          const float4 b = reinterpret_cast<const float4*>(p)[1];
+          x[0] = rel_pos_f(b.x, AB.sf[0], AB.lo[0], AB.hi[0]);
+          x[1] = rel_pos_f(b.y, AB.sf[1], AB.lo[1], AB.hi[1]);
+          x[2] = rel_pos_f(b.z, AB.sf[2], AB.lo[2], AB.hi[2]);
+        };
+        {
+          long long Qo[3] = {0, 0, 0};
+          if (has_ovf)
+            for (uint32_t j = 0; j < novf; ++j)
+              if (ovf_cell[j] == (uint32_t)cell) {
+                float x[3];
+                rel_of(ovf + j, x);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) Qo[q] += fix32_rne(x[q]);
+              }
+          float rcm[3] = {0.0f, 0.0f, 0.0f};
+          if (n > 0) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              rcm[q] = (split_sum_to_float(AG.qh[q][lane], AG.ql[q][lane], Qo[q]) * 0x1p-32f) /
+                       small_to_float((int)n);
+          }
+          AG.rc[lane] = make_float4(rcm[0], rcm[1], rcm[2], 0.0f);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            AG.lh[k][lane] = 0;
+            AG.ll[k][lane] = 0;
+          }
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            AG.ph[k][lane] = 0;
+            AG.pl[k][lane] = 0;
+          }
+        }
+        __syncwarp();
+        // r_c x (v - v') and the inertia-tensor entries of a member of cell o,
+        // v' by the same operations as pass 2
+        auto terms = [&](const float v[3], const float x[3], int o, float tm[9]) {
+          const float4 pa = W.prm[0][o], pb = W.prm[1][o], c = AG.rc[o];
+          const float nn[3] = {pb.x, pb.y, pb.z};
+          const float uu[3] = {pa.x, pa.y, pa.z};
+          float d[3], rr[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) d[q] = v[q] - uu[q];
+          rotate(nn, H.ca, H.sa, H.omc, d, rr);
+          float dv[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) dv[q] = v[q] - (uu[q] + rr[q]);
+          const float rc[3] = {x[0] - c.x, x[1] - c.y, x[2] - c.z};
+          tm[0] = rc[1] * dv[2] - rc[2] * dv[1];
+          tm[1] = rc[2] * dv[0] - rc[0] * dv[2];
+          tm[2] = rc[0] * dv[1] - rc[1] * dv[0];
+          tm[3] = rc[1] * rc[1] + rc[2] * rc[2];
+          tm[4] = rc[0] * rc[1];
+          tm[5] = rc[0] * rc[2];
+          tm[6] = rc[0] * rc[0] + rc[2] * rc[2];
+          tm[7] = rc[1] * rc[2];
+          tm[8] = rc[0] * rc[0] + rc[1] * rc[1];
+        };
+        bool slow_a = false;
+        for (int sbase = 0; sbase < N; sbase += STAGE) {
+          const int cnt = min(STAGE, N - sbase);
+          if (N > STAGE) stage(sbase, cnt);  // else still staged from pass 1
+          int Ha[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, La[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+          share(sbase, cnt, [&](int o, int js, bool last) {
+            const float v[3] = {W.sv[0][js], W.sv[1][js], W.sv[2][js]};
+            const float x[3] = {AG.sr[0][js], AG.sr[1][js], AG.sr[2][js]};
+            float tm[9];
+            terms(v, x, o, tm);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+              int h, l;
+              if (!split32(tm[k], h, l)) {
+                slow_a = true;
+                h = 0;
+                l = 0;
+              }
+              Ha[k] += h;
+              La[k] += l;
+            }
+            if (last) {
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                atomicAdd(&AG.lh[k][o], Ha[k]);
+                atomicAdd(&AG.ll[k][o], La[k]);
+              }
+#pragma unroll
+              for (int k = 0; k < 6; ++k) {
+                atomicAdd(&AG.ph[k][o], Ha[3 + k]);
+                atomicAdd(&AG.pl[k][o], La[3 + k]);
+              }
+#pragma unroll
+              for (int k = 0; k < 9; ++k) {
+                Ha[k] = 0;
+                La[k] = 0;
+              }
+            }
+          });
+          __syncwarp();
+        }
+        const bool exact_a = __any_sync(FULL, slow_a);  // a term of 1024 or more
+        if (n > 0) {
+          long long Lo[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+          auto add_terms = [&](const R* p) {
+            const float4 a = reinterpret_cast<const float4*>(p)[0];
+            const float v[3] = {a.x, a.y, a.z};
+            float x[3], tm[9];
+            rel_of(p, x);
+            terms(v, x, lane, tm);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Lo[k] += fix32_rne(tm[k]);
+          };
+          if (exact_a)
+            for (int k = 0; k < nrow; ++k) add_terms(rows + (size_t)lane * K + k);
+          if (has_ovf)
+            for (uint32_t j = 0; j < novf; ++j)
+              if (ovf_cell[j] == (uint32_t)cell) add_terms(ovf + j);
+          float dL[3], P6[6], om[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float tot = exact_a ? i64_to_float(Lo[k])
+                                      : split_sum_to_float(AG.lh[k][lane], AG.ll[k][lane], Lo[k]);
+            dL[k] = H.m * (tot * 0x1p-32f);
+          }
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            const float tot = exact_a ? i64_to_float(Lo[3 + k])
+                                      : split_sum_to_float(AG.ph[k][lane], AG.pl[k][lane], Lo[3 + k]);
+            const float e = H.m * (tot * 0x1p-32f);
+            P6[k] = (k == 1 || k == 2 || k == 4) ? -e : e;
+          }
+          solve_omega<float>((int)n, P6, dL, om);
+          AG.om[lane] = make_float4(om[0], om[1], om[2], 0.0f);
+        }
+        __syncwarp();
+      }
     }
 
     // ---- pass 2: collide (Eq. srd), stream (Eq. stream), bin (Sec. 3.4) ----
@@ -662,6 +868,15 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
         rotate(nn, H.ca, H.sa, H.omc, d, rr);
 #pragma unroll
         for (int q = 0; q < 3; ++q) w[q] = uu[q] + (THERMO ? pa.w * rr[q] : rr[q]);
+        if (ANG) {  // v'' = v' + omega x r_c
+          const float4 c = AG.rc[o], om = AG.om[o];
+          const float rc[3] = {rel_pos_f(r[0], AB.sf[0], AB.lo[0], AB.hi[0]) - c.x,
+                               rel_pos_f(r[1], AB.sf[1], AB.lo[1], AB.hi[1]) - c.y,
+                               rel_pos_f(r[2], AB.sf[2], AB.lo[2], AB.hi[2]) - c.z};
+          w[0] = w[0] + (om.y * rc[2] - om.z * rc[1]);
+          w[1] = w[1] + (om.z * rc[0] - om.x * rc[2]);
+          w[2] = w[2] + (om.x * rc[1] - om.y * rc[0]);
+        }
       }
       if (MODE == MODE_C) return 0u;
       // periodic box; the additions of zero keep the operation sequence of
@@ -785,9 +1000,9 @@ __global__ void __launch_bounds__(BLOCK, AT ? 2 : ((THERMO || BEADS) ? 3 : 4)) k
   }
 }
 
-template <bool TH, int MODE, bool FO, bool BE, bool AT>
+template <bool TH, int MODE, bool FO, bool BE, bool AT, bool ANG = false>
 static void* warp_fn() {
-  return (void*)k_cells_warp<TH, MODE, FO, BE, AT>;
+  return (void*)k_cells_warp<TH, MODE, FO, BE, AT, ANG>;
 }
 
 template <int MODE, bool BE>
@@ -798,32 +1013,36 @@ static void* warp_variant_mb(bool thermo, bool force, bool at) {
 }
 
 template <int MODE>
-static void* warp_variant_mode(bool thermo, bool force, bool beads, bool at) {
+static void* warp_variant_mode(bool thermo, bool force, bool beads, bool at, bool ang) {
+  if (ang) return force ? warp_fn<false, MODE, true, false, false, true>()
+                        : warp_fn<false, MODE, false, false, false, true>();
   return beads ? warp_variant_mb<MODE, true>(thermo, force, at)
                : warp_variant_mb<MODE, false>(thermo, force, at);
 }
 
-static void* warp_variant(bool thermo, bool force, bool beads, bool at, int mode) {
-  if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force, beads, at);
-  if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force, beads, at);
-  return warp_variant_mode<MODE_C>(thermo, force, beads, at);
+// ang: the angular-momentum correction (SRD without thermostat or beads only).
+static void* warp_variant(bool thermo, bool force, bool beads, bool at, bool ang, int mode) {
+  if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force, beads, at, ang);
+  if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force, beads, at, ang);
+  return warp_variant_mode<MODE_C>(thermo, force, beads, at, ang);
 }
 
-int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode) {
-  const void* fn = warp_variant(thermo, force, beads, at, mode);
-  const size_t smem = block_smem(beads, at);
+int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, bool ang, int mode) {
+  const void* fn = warp_variant(thermo, force, beads, at, ang, mode);
+  const size_t smem = block_smem(beads, at, ang);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, smem);
   return nb;
 }
 
-void launch_cells_warp(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,
-                       const int2* spans, int nspans, int grid, int* err, cudaStream_t s) {
+void launch_cells_warp(bool thermo, bool force, bool beads, bool at, bool ang, int mode,
+                       const BoxDev* boxes, const int2* spans, int nspans, int grid, int* err,
+                       cudaStream_t s) {
   if (nspans <= 0) return;
   void* args[] = {(void*)&boxes, (void*)&spans, (void*)&nspans, (void*)&err};
-  cudaLaunchKernel(warp_variant(thermo, force, beads, at, mode), dim3(grid), dim3(BLOCK), args,
-                   block_smem(beads, at), s);
+  cudaLaunchKernel(warp_variant(thermo, force, beads, at, ang, mode), dim3(grid), dim3(BLOCK), args,
+                   block_smem(beads, at, ang), s);
 }
 
 }  // namespace mpcd

@@ -21,9 +21,12 @@ void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const 
 // beads: the box has solute beads; at: Andersen-thermostat rule (Eq. at)
 // instead of the rotation (thermo is then false).
 constexpr int WARP_MAX_K = 448;
-int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode);
-void launch_cells_warp(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,
-                       const int2* spans, int nspans, int grid, int* err, cudaStream_t s);
+// ang (mixed model, SRD without thermostat or beads): the angular-momentum
+// correction.
+int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, bool ang, int mode);
+void launch_cells_warp(bool thermo, bool force, bool beads, bool at, bool ang, int mode,
+                       const BoxDev* boxes, const int2* spans, int nspans, int grid, int* err,
+                       cudaStream_t s);
 // The FP64 model's counterpart (k_cells_warp_d.cu), same conditions.
 int cells_warpd_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode);
 void launch_cells_warpd(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,

@@ -114,3 +114,23 @@ def test_angular_rejects_walls_and_solute():
         pkg.Box(n=(4, 4, 4), angular=True, walls_z=True)
     with pytest.raises(pkg.MpcdError):
         pkg.Box(n=(4, 4, 4), angular=True, chain_len=4, md_substeps=1, solute_mass=5.0)
+
+
+def test_angular_mixed_large_velocities_exact():
+    # members with |v| >= 1024: the momentum sums and the terms r_c x (v - v')
+    # leave the int32 split and take the exact int64 paths
+    s = inputs.solvent((6, 6, 6), 5, seed=12, mixed=True)
+    vel = s.vel.copy()
+    rng = np.random.default_rng(1)
+    idx = rng.choice(len(vel), 40, replace=False)
+    vel[idx] = rng.uniform(1024.0, 1500.0, (40, 3)) * rng.choice([-1.0, 1.0], (40, 3))
+    vel = vel.astype(np.float32).astype(np.float64)
+    run((6, 6, 6), s.pos, vel, "mixed", 2, 12, "srd")
+
+
+def test_angular_two_member_and_lone_cells():
+    # a sparse box: most cells hold one or two members (the rank-two branch)
+    s = inputs.solvent((8, 8, 8), 1.5, seed=15, mixed=True)
+    run((8, 8, 8), s.pos, s.vel, "mixed", 3, 15, "srd")
+    s = inputs.solvent((8, 8, 8), 1.5, seed=15)
+    run((8, 8, 8), s.pos, s.vel, "fp64", 3, 15, "srd")
