@@ -328,7 +328,7 @@ def main():
     dom_ms = phases[dom]
     achieved = step_bytes * s.pos.shape[0] / (dom_ms * 1e-3) / 1e9
     # the warp-spread kernel runs mixed-model boxes without walls
-    if cfg.get("angular") and not (cfg["precision"] == "mixed" and not cfg["thermostat"]
+    if cfg.get("angular") and not (cfg["precision"] == "mixed"
                                    and cfg.get("collision", "srd") == "srd"):
         kname = "k_cells"  # one thread per cell
     else:

@@ -311,9 +311,10 @@ struct Engine {
     for (int m = 0; m < 3; ++m)
       for (int v = 0; v < NVAR; ++v) {
         const bool at = (v & 16) != 0, ang = (v & 32) != 0;
-        if ((v & 4) && ang)  // warp-spread angular correction: mixed SRD, no thermostat or beads
-          cells_bps[m][v] = (mixed && !(v & (1 | 8 | 16)))
-                                ? cells_warp_blocks_per_sm(false, (v & 2) != 0, false, false, true, m)
+        if ((v & 4) && ang)  // warp-spread angular correction: mixed SRD without beads
+          cells_bps[m][v] = (mixed && !(v & (8 | 16)))
+                                ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, false, false,
+                                                           true, m)
                                 : 1;
         else if ((v & 4) && !(at && (v & 1)))
           cells_bps[m][v] =
@@ -453,7 +454,7 @@ struct Engine {
       const bool at = d.collision == RULE_AT;
       int variant = (d.thermostat ? 1 : 0) | ((d.walls || d.nbead > 0) ? 2 : 0) | (at ? 16 : 0) |
                     (d.angular ? 32 : 0);
-      const bool warp_ang = mixed && !d.thermostat && !at && d.nbead == 0;
+      const bool warp_ang = mixed && !at && d.nbead == 0;
       if ((!d.angular || warp_ang) && !d.walls && d.K <= WARP_MAX_K &&
           std::max(d.n[0], std::max(d.n[1], d.n[2])) < (1 << 22)) {
         const bool force = d.g[0] != 0.0 || d.g[1] != 0.0 || d.g[2] != 0.0;

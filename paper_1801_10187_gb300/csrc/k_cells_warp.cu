@@ -152,7 +152,7 @@ constexpr size_t SPAN_SMEM = (sizeof(SpanParams) + 15) & ~(size_t)15;
 constexpr size_t BLOCK_SMEM = SPAN_SMEM + WARPS * WARP_SMEM;
 constexpr size_t BLOCK_SMEM_BEADS = BLOCK_SMEM + WARPS * sizeof(BeadShared);
 
-// Angular-momentum correction (SRD without thermostat or beads): the float
+// Angular-momentum correction (SRD without beads): the float
 // frame of the collision step's shift (per block), and per warp the staged
 // relative positions of the members, split sums per cell of the positions,
 // of r_c x (v - v') and of the six inertia-tensor entries, and per cell the
@@ -213,8 +213,9 @@ __device__ __forceinline__ float wrap_fast(float x, float L) {
 // AT selects the Andersen rule (then THERMO is false): its two Box-Muller
 // draws per member want registers for independent chains, and its cache of
 // random velocities wants shared memory, so it runs two blocks per SM.
-// ANG adds the angular-momentum correction to SRD (then THERMO, BEADS and AT
-// are false); its shared memory allows two blocks per SM.
+// ANG adds the angular-momentum correction to SRD, with or without the
+// thermostat (then BEADS and AT are false); its shared memory allows two
+// blocks per SM.
 template <bool THERMO, int MODE, bool FORCE, bool BEADS, bool AT, bool ANG>
 __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 3 : 4)) k_cells_warp(const BoxDev* __restrict__ boxes,
                                                          const int2* __restrict__ spans,
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
           rotate(nn, H.ca, H.sa, H.omc, d, rr);
           float dv[3];
 #pragma unroll
-          for (int q = 0; q < 3; ++q) dv[q] = v[q] - (uu[q] + rr[q]);
+          for (int q = 0; q < 3; ++q) dv[q] = v[q] - (uu[q] + (THERMO ? pa.w * rr[q] : rr[q]));
           const float rc[3] = {x[0] - c.x, x[1] - c.y, x[2] - c.z};
           tm[0] = rc[1] * dv[2] - rc[2] * dv[1];
           tm[1] = rc[2] * dv[0] - rc[0] * dv[2];
@@ -1014,13 +1015,15 @@ static void* warp_variant_mb(bool thermo, bool force, bool at) {
 
 template <int MODE>
 static void* warp_variant_mode(bool thermo, bool force, bool beads, bool at, bool ang) {
+  if (ang && thermo) return force ? warp_fn<true, MODE, true, false, false, true>()
+                                  : warp_fn<true, MODE, false, false, false, true>();
   if (ang) return force ? warp_fn<false, MODE, true, false, false, true>()
                         : warp_fn<false, MODE, false, false, false, true>();
   return beads ? warp_variant_mb<MODE, true>(thermo, force, at)
                : warp_variant_mb<MODE, false>(thermo, force, at);
 }
 
-// ang: the angular-momentum correction (SRD without thermostat or beads only).
+// ang: the angular-momentum correction (SRD without beads only).
 static void* warp_variant(bool thermo, bool force, bool beads, bool at, bool ang, int mode) {
   if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force, beads, at, ang);
   if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force, beads, at, ang);

@@ -21,8 +21,7 @@ void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const 
 // beads: the box has solute beads; at: Andersen-thermostat rule (Eq. at)
 // instead of the rotation (thermo is then false).
 constexpr int WARP_MAX_K = 448;
-// ang (mixed model, SRD without thermostat or beads): the angular-momentum
-// correction.
+// ang (mixed model, SRD without beads): the angular-momentum correction.
 int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, bool ang, int mode);
 void launch_cells_warp(bool thermo, bool force, bool beads, bool at, bool ang, int mode,
                        const BoxDev* boxes, const int2* spans, int nspans, int grid, int* err,
