@@ -70,8 +70,9 @@ typedef enum { MPCD_FP64 = 0, MPCD_MIXED = 1 } mpcd_precision;
  * about that centre (v before, v' after the rule), so each cell keeps its
  * angular momentum; a two-member or collinear cell takes omega = 2 dL /
  * tr(Pi).  The mixed model sums in int64 fixed point and solves in float.
- * Not with walls or solute (EINVAL).  These boxes run on a kernel with one
- * thread per cell. */
+ * Not with walls or solute (EINVAL).  Mixed-model SRD boxes take it in the
+ * fused warp-spread pass; the Andersen rule and FP64 on a kernel with one
+ * thread per cell (slower; same results). */
 typedef enum { MPCD_SRD = 0, MPCD_AT = 1 } mpcd_collision;
 
 /* SRD parameters (Sec. 2; Sec. 4 benchmark values in brackets).  Plain
