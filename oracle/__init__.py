@@ -65,6 +65,8 @@ class _Params(ctypes.Structure):
         ("bond_r0", ctypes.c_double),
         ("angular", ctypes.c_int32),
         ("pad2_", ctypes.c_int32),
+        ("lj_epsilon", ctypes.c_double),
+        ("lj_sigma", ctypes.c_double),
     ]
 
 
@@ -87,6 +89,9 @@ def _load():
         _lib.oracle_gamma_draw.argtypes = [u64, u64, ctypes.c_uint32, i32, d, i32, P(d)]
         _lib.oracle_gamma_draw.restype = i32
         _lib.oracle_at_draw.argtypes = [u64, u64, ctypes.c_uint32, i32, d, i32, P(d)]
+        _lib.oracle_solute_forces.argtypes = [P(_Params), i64, P(d), P(d)]
+        _lib.oracle_solute_energy.argtypes = [P(_Params), i64, P(d)]
+        _lib.oracle_solute_energy.restype = d
         _lib.oracle_step.argtypes = [P(_Params), i64, P(d), P(d), i64, P(d), P(d), P(u64), i64,
                                      P(i32), P(i32)]
         _lib.oracle_step.restype = i32
@@ -120,6 +125,8 @@ class Params:
     bond_r0: float = 0.0
     collision: int = SRD
     angular: bool = False
+    lj_epsilon: float = 0.0
+    lj_sigma: float = 0.0
 
     def c(self) -> _Params:
         p = _Params()
@@ -141,6 +148,8 @@ class Params:
         p.bond_r0 = self.bond_r0
         p.collision = int(self.collision)
         p.angular = int(bool(self.angular))
+        p.lj_epsilon = float(self.lj_epsilon)
+        p.lj_sigma = float(self.lj_sigma)
         return p
 
 
@@ -195,6 +204,20 @@ def at_draw(seed: int, t: int, tag: int, kind: int, sigma: float, precision: int
     dv = np.zeros(3)
     _load().oracle_at_draw(seed, t, tag, kind, sigma, precision, _dptr(dv))
     return dv
+
+
+def solute_forces(params: Params, r: np.ndarray) -> np.ndarray:
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    F = np.zeros_like(r)
+    p = params.c()
+    _load().oracle_solute_forces(ctypes.byref(p), r.shape[0], _dptr(r), _dptr(F))
+    return F
+
+
+def solute_energy(params: Params, r: np.ndarray) -> float:
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    p = params.c()
+    return float(_load().oracle_solute_energy(ctypes.byref(p), r.shape[0], _dptr(r)))
 
 
 def num_cells(params: Params) -> int:

@@ -443,17 +443,85 @@ static void bond_forces(const oracle_params* p, int64_t nb, const double* r, dou
   }
 }
 
+/* Non-bonded solute forces (Sec. 4.3 uses a bead-spring model with
+ * non-bonded pair forces from a neighbour list; the potential is only cited).
+ * Reading: the Weeks-Chandler-Andersen repulsion between every pair of beads,
+ * U(r) = 4 eps ((sigma/r)^12 - (sigma/r)^6) + eps for r < 2^(1/6) sigma,
+ * 0 beyond, minimum-image distances; the force on bead i from j is
+ * (24 eps / r^2) (2 (sigma/r)^12 - (sigma/r)^6) (r_i - r_j).  Every pair is
+ * visited (no neighbour list here). */
+static void pair_forces(const oracle_params* p, int64_t nb, const double* r, double* F) {
+  double L[3] = {(double)p->n[0], (double)p->n[1], (double)p->n[2]};
+  double eps = p->lj_epsilon, s2 = p->lj_sigma * p->lj_sigma;
+  double rc2 = pow(2.0, 1.0 / 3.0) * s2;
+  for (int64_t i = 0; i < nb; ++i) {
+    for (int64_t j = 0; j < nb; ++j) {
+      if (j == i) continue;
+      double d[3];
+      for (int k = 0; k < 3; ++k) {
+        d[k] = r[3 * j + k] - r[3 * i + k];
+        d[k] = d[k] - L[k] * nearbyint(d[k] / L[k]);
+      }
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (!(r2 < rc2)) continue;
+      double q = s2 / r2;
+      double q6 = q * q * q;
+      double g = 24.0 * eps * q6 * (2.0 * q6 - 1.0) / r2;
+      for (int k = 0; k < 3; ++k) F[3 * i + k] -= g * d[k];
+    }
+  }
+}
+
+static void solute_forces(const oracle_params* p, int64_t nb, const double* r, double* F) {
+  bond_forces(p, nb, r, F);
+  if (p->lj_epsilon > 0.0) pair_forces(p, nb, r, F);
+}
+
+/* Potential energy of the solute: harmonic bonds k/2 (r - r0)^2 and, when
+ * on, the WCA repulsion of every pair (each pair once). */
+double oracle_solute_energy(const oracle_params* p, int64_t nb, const double* r) {
+  double L[3] = {(double)p->n[0], (double)p->n[1], (double)p->n[2]};
+  int64_t cl = p->chain_len > 0 ? p->chain_len : 1;
+  double U = 0.0;
+  for (int64_t i = 0; i < nb; ++i) {
+    for (int64_t j = i + 1; j < nb; ++j) {
+      double d[3];
+      for (int k = 0; k < 3; ++k) {
+        d[k] = r[3 * j + k] - r[3 * i + k];
+        d[k] = d[k] - L[k] * nearbyint(d[k] / L[k]);
+      }
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      if (j == i + 1 && (i % cl) != cl - 1) {
+        double x = sqrt(r2) - p->bond_r0;
+        U += 0.5 * p->bond_k * x * x;
+      }
+      if (p->lj_epsilon > 0.0) {
+        double s2 = p->lj_sigma * p->lj_sigma;
+        if (r2 < pow(2.0, 1.0 / 3.0) * s2) {
+          double q6 = pow(s2 / r2, 3.0);
+          U += 4.0 * p->lj_epsilon * (q6 * q6 - q6) + p->lj_epsilon;
+        }
+      }
+    }
+  }
+  return U;
+}
+
+void oracle_solute_forces(const oracle_params* p, int64_t nb, const double* r, double* F) {
+  solute_forces(p, nb, r, F);
+}
+
 static void md_substeps(const oracle_params* p, int64_t nb, double* r, double* v) {
   double L[3] = {(double)p->n[0], (double)p->n[1], (double)p->n[2]};
   double h = p->dt / (double)p->md_substeps;
   double hh = (0.5 * h) / p->solute_mass;
   double* F = (double*)malloc(sizeof(double) * 3 * (size_t)nb);
-  bond_forces(p, nb, r, F);
+  solute_forces(p, nb, r, F);
   for (int s = 0; s < p->md_substeps; ++s) {
     for (int64_t i = 0; i < 3 * nb; ++i) v[i] = v[i] + hh * F[i];
     for (int64_t i = 0; i < nb; ++i)
       for (int k = 0; k < 3; ++k) r[3 * i + k] = wrap_d(r[3 * i + k] + h * v[3 * i + k], L[k]);
-    bond_forces(p, nb, r, F);
+    solute_forces(p, nb, r, F);
     for (int64_t i = 0; i < 3 * nb; ++i) v[i] = v[i] + hh * F[i];
   }
   free(F);
@@ -1044,6 +1112,7 @@ static int32_t check_params(const oracle_params* p, int64_t n, int64_t nb) {
   if (p->collision != ORACLE_SRD && p->collision != ORACLE_AT) return -1;
   if (p->collision == ORACLE_AT && (p->thermostat || p->walls_z)) return -1;
   if (p->angular && (p->walls_z || nb > 0)) return -1;
+  if (p->lj_epsilon < 0.0 || (p->lj_epsilon > 0.0 && !(p->lj_sigma > 0.0))) return -1;
   if (nb > 0 && (p->chain_len < 1 || nb % p->chain_len != 0 || p->md_substeps < 1 ||
                  !(p->solute_mass > 0.0)))
     return -1;

@@ -20,7 +20,8 @@
  *                          that restores its angular momentum
  *   Sec. 3.6             : cylindrical-projection axis, Marsaglia-Tsang Gamma
  *                          draw with a Box-Muller normal, xi = 1 if Nc < 2
- *   Sec. 2 / Sec. 3.6    : solute beads (velocity Verlet, harmonic bonds)
+ *   Sec. 2 / Sec. 3.6    : solute beads (velocity Verlet, harmonic bonds, and
+ *                          optionally a non-bonded pair repulsion, Sec. 4.3)
  *                          binned and collided with the solvent
  *   Sec. 3.5 (last par.) : net momentum / energy / temperature observables
  * Walls with bounce-back and a body force are not given in the paper (Sec. 5
@@ -75,6 +76,8 @@ typedef struct {
   double bond_r0;        /* harmonic bond rest length                       */
   int32_t angular;       /* 1 = conserve each cell's angular momentum        */
   int32_t pad2_;
+  double lj_epsilon;     /* solute non-bonded WCA repulsion: epsilon (0 off) */
+  double lj_sigma;       /* and sigma (cutoff 2^(1/6) sigma)                 */
 } oracle_params;
 
 /* Philox4x32-10 (Salmon et al., SC11) on one counter block. */
@@ -122,6 +125,12 @@ void oracle_at_draw(uint64_t seed, uint64_t t, uint32_t tag, int32_t kind, doubl
 int32_t oracle_step(const oracle_params* p, int64_t n, double* pos, double* vel,
                     int64_t nb, double* spos, double* svel, uint64_t* step,
                     int64_t nsteps, int32_t* cell_out, int32_t* count_out);
+
+/* Solute forces (bonds and, with lj_epsilon > 0, the WCA pair repulsion)
+ * on nb beads at r (nb x 3; chains of chain_len consecutive beads), and the
+ * potential energy they derive from. */
+void oracle_solute_forces(const oracle_params* p, int64_t nb, const double* r, double* F);
+double oracle_solute_energy(const oracle_params* p, int64_t nb, const double* r);
 
 /* Number of cells of the collision grid (n_z + 2 layers when walls_z). */
 int64_t oracle_num_cells(const oracle_params* p);
