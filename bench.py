@@ -70,19 +70,27 @@ def box_kwargs(cfg):
               angular=cfg.get("angular", False))
     if cfg.get("n_chains"):
         kw.update(chain_len=cfg["chain_len"], md_substeps=cfg["md_substeps"],
-                  solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"])
+                  solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"],
+                  lj_epsilon=cfg.get("lj_epsilon", 0.0), lj_sigma=cfg.get("lj_sigma", 0.0))
     return kw
 
 
-def make_state(cfg, n=None, seed_offset=0):
+def make_chains(cfg, n, n_chains, seed):
+    if cfg.get("lj_epsilon"):  # beads that repel start apart
+        return inputs.avoiding_chains(n, n_chains, cfg["chain_len"], cfg["bond_r0"],
+                                      0.9 * cfg["lj_sigma"], kT=cfg["kT"],
+                                      bead_mass=cfg["bead_mass"], seed=seed)
+    return inputs.chains(n, n_chains, cfg["chain_len"], cfg["bond_r0"], kT=cfg["kT"],
+                         bead_mass=cfg["bead_mass"], seed=seed)
+
+
+def make_state(cfg, n=None, seed_offset=0, with_chains=True):
     n = n or cfg["n"]
     s = inputs.solvent(n, cfg["density"], kT=cfg["kT"], seed=cfg["seed"] + seed_offset,
                        mixed=cfg["precision"] == "mixed")
     sp = sv = None
-    if cfg.get("n_chains"):
-        sp, sv = inputs.chains(n, cfg["n_chains"], cfg["chain_len"], cfg["bond_r0"],
-                               kT=cfg["kT"], bead_mass=cfg["bead_mass"],
-                               seed=cfg["seed"] + 1000 + seed_offset)
+    if cfg.get("n_chains") and with_chains:
+        sp, sv = make_chains(cfg, n, cfg["n_chains"], cfg["seed"] + 1000 + seed_offset)
     return s, sp, sv
 
 
@@ -153,12 +161,19 @@ def oracle_rate(cfg, budget_s, steps=None, warmup=0):
     nsteps = steps if steps else 3
     want_ps = budget_s * 1e9 / ns_per_ps / max(1, nsteps + warmup)
     cells = min(full_cells, max(27, int(want_ps / cfg["density"])))
+    if cfg.get("lj_epsilon"):
+        # the oracle's pair repulsion visits every pair of beads in every MD
+        # substep: keep the sample's beads (at the workload's bead density)
+        # within the budget, about 10 ns per pair visit
+        nb_max = math.sqrt(budget_s / max(1, nsteps + warmup) / cfg["md_substeps"] / 1e-8)
+        nb_full = cfg["n_chains"] * cfg["chain_len"]
+        cells = min(cells, max(27, int(full_cells * nb_max / nb_full)))
     if cells < full_cells:
         edge = max(3, int(round(cells ** (1 / 3))))
         n = (edge, edge, edge)
     else:
         n = tuple(cfg["n"])
-    s, sp, sv = make_state(cfg, n=n)
+    s, sp, sv = make_state(cfg, n=n, with_chains=False)
     prec = oracle.MIXED if cfg["precision"] == "mixed" else oracle.FP64
     okw = dict(n=n, dt=cfg["dt"], alpha_deg=cfg["alpha_deg"], kT=cfg["kT"], seed=cfg["seed"],
                thermostat=cfg["thermostat"], precision=prec,
@@ -166,10 +181,10 @@ def oracle_rate(cfg, budget_s, steps=None, warmup=0):
                angular=bool(cfg.get("angular", False)))
     if cfg.get("n_chains"):
         nch = max(1, int(round(cfg["n_chains"] * np.prod(n) / full_cells)))
-        sp, sv = inputs.chains(n, nch, cfg["chain_len"], cfg["bond_r0"], kT=cfg["kT"],
-                               bead_mass=cfg["bead_mass"], seed=cfg["seed"] + 1000)
+        sp, sv = make_chains(cfg, n, nch, cfg["seed"] + 1000)
         okw.update(chain_len=cfg["chain_len"], md_substeps=cfg["md_substeps"],
-                   solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"])
+                   solute_mass=cfg["bead_mass"], bond_k=cfg["bond_k"], bond_r0=cfg["bond_r0"],
+                   lj_epsilon=cfg.get("lj_epsilon", 0.0), lj_sigma=cfg.get("lj_sigma", 0.0))
     p = oracle.Params(**okw)
     st = oracle.State(s.pos, s.vel, sp if sp is not None else np.zeros((0, 3)),
                       sv if sv is not None else np.zeros((0, 3)))
@@ -386,7 +401,10 @@ def main():
         rate, sample, dt, nsteps = oracle_rate(cfg, 20.0)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
-    launches = (LAUNCHES_PER_STEP_SOLUTE if cfg.get("n_chains") else LAUNCHES_PER_STEP) * K
+    per_step = LAUNCHES_PER_STEP_SOLUTE if cfg.get("n_chains") else LAUNCHES_PER_STEP
+    if cfg.get("lj_epsilon"):  # neighbour-list build (3), first force, 3 per MD substep
+        per_step += 4 + 3 * cfg["md_substeps"]
+    launches = per_step * K
     config["l2"] = (f"state {s.pos.shape[0] * 6 * es / 1e6:.0f} MB > 129 MB L2 (inputs larger "
                     "than L2; no flush)")
     if rank == 0:

@@ -102,7 +102,21 @@ typedef struct {
   double bond_r0;        /* solute: harmonic bond rest length r0             */
   int32_t angular;       /* 1: conserve each cell's angular momentum (below) */
   int32_t reserved1;
+  double lj_epsilon;     /* solute: non-bonded WCA repulsion epsilon (0 off) */
+  double lj_sigma;       /* solute: WCA sigma; cutoff 2^(1/6) sigma; needs    */
+                         /* 2^(1/6) sigma + 0.4 <= 1 (neighbour-list buffer)  */
 } mpcd_params;
+
+/* Non-bonded solute forces (Sec. 4.3: the paper's polymer benchmark uses
+ * pair forces from a neighbour list with a 0.4 a buffer and cites the
+ * bead-spring potential): with lj_epsilon > 0 every pair of beads repels by
+ * the Weeks-Chandler-Andersen potential U(r) = 4 eps ((sigma/r)^12 -
+ * (sigma/r)^6) + eps for r < 2^(1/6) sigma (minimum-image distances), added
+ * to the bond forces in every velocity-Verlet substep.  The neighbour list
+ * (buffer 0.4) is built every collision step and rebuilt within it as soon as
+ * a bead has moved more than half the buffer; a bead with more than 64
+ * neighbours is reported as MPCD_EDEVICE.  Needs n_k >= 3 and
+ * 2^(1/6) sigma + 0.4 <= 1 (EINVAL). */
 
 /* Observables of the current state (Sec. 3.5, last paragraph). */
 typedef struct {

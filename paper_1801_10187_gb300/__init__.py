@@ -55,6 +55,8 @@ class _Params(ctypes.Structure):
         ("bond_r0", ctypes.c_double),
         ("angular", ctypes.c_int32),
         ("reserved1", ctypes.c_int32),
+        ("lj_epsilon", ctypes.c_double),
+        ("lj_sigma", ctypes.c_double),
     ]
 
 
@@ -146,7 +148,7 @@ def make_params(n=(10, 10, 10), dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=
                 thermostat=False, sort_period=0, walls_z=False, body_force=(0.0, 0.0, 0.0),
                 virt_density=0.0, precision="mixed", chain_len=0, md_substeps=0,
                 solute_mass=1.0, bond_k=0.0, bond_r0=0.0, alpha=None,
-                collision="srd", angular=False) -> _Params:
+                collision="srd", angular=False, lj_epsilon=0.0, lj_sigma=0.0) -> _Params:
     p = _Params()
     p.n[:] = [int(x) for x in n]
     p.precision = MIXED if precision in ("mixed", MIXED) else FP64
@@ -168,6 +170,8 @@ def make_params(n=(10, 10, 10), dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=
     p.bond_r0 = float(bond_r0)
     p.collision = AT if collision in ("at", AT) else SRD
     p.angular = int(bool(angular))
+    p.lj_epsilon = float(lj_epsilon)
+    p.lj_sigma = float(lj_sigma)
     return p
 
 

@@ -81,6 +81,9 @@ size_t footprint_bytes(const mpcd_params& p, int64_t nsol, int64_t nbead) {
     b += (size_t)nbead * (9 * sizeof(double) + 2 * sizeof(int32_t) + sizeof(uint64_t) +
                           sizeof(uint32_t));
     b += (size_t)ng * sizeof(uint32_t) + (size_t)(ng + 1) * sizeof(uint32_t);
+    if (p.lj_epsilon > 0.0)  // neighbour list: buckets, next, key, count, list, build r, forces
+      b += (size_t)(2 * ((nbead + PTILE - 1) / PTILE) * PTILE) * sizeof(int32_t) +
+           (size_t)nbead * (3 * sizeof(int32_t) + NL_MAX * sizeof(int32_t) + 6 * sizeof(double));
   }
   return b;
 }
@@ -107,6 +110,14 @@ int validate(const mpcd_params* p, int precision_expected) {
     return fail(MPCD_EINVAL, "the Andersen rule thermostats by itself: no thermostat flag, no walls");
   if (p->angular && (p->walls_z || p->chain_len > 0))
     return fail(MPCD_EINVAL, "angular momentum conservation takes neither walls nor solute");
+  if (!(p->lj_epsilon >= 0.0)) return fail(MPCD_EINVAL, "lj_epsilon must be >= 0");
+  if (p->lj_epsilon > 0.0) {
+    if (!(p->lj_sigma > 0.0) || std::pow(2.0, 1.0 / 6.0) * p->lj_sigma + NL_SKIN > 1.0)
+      return fail(MPCD_EINVAL, "WCA repulsion needs 0 < 2^(1/6) lj_sigma <= 0.6 (cutoff plus the "
+                               "0.4 neighbour-list buffer within one cell)");
+    if (p->n[0] < 3 || p->n[1] < 3 || p->n[2] < 3)
+      return fail(MPCD_EINVAL, "WCA repulsion needs at least 3 cells per axis");
+  }
   if (p->chain_len < 0 || p->chain_len > 1024) return fail(MPCD_EINVAL, "chain_len in [0, 1024]");
   if (p->chain_len > 0 && (p->md_substeps < 1 || !(p->solute_mass > 0.0)))
     return fail(MPCD_EINVAL, "solute needs md_substeps >= 1 and solute_mass > 0");
@@ -290,6 +301,7 @@ struct Engine {
   int* d_err = nullptr;
   double* d_partials = nullptr;
   bool any_beads = false;
+  int wca_substeps = 0;  // most MD substeps of a box with the WCA repulsion (0: none)
   int cells_bps[3][NVAR] = {};
 
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // MODE_P, MODE_F, MODE_C
@@ -420,6 +432,7 @@ struct Engine {
       if (h & ERR_GAMMA_CAP) m += "thermostat Gamma sampler rejected 64 draws; ";
       if (h & ERR_CELL_RANGE) m += "a position was not finite (cell id clamped); ";
       if (h & ERR_OVERFLOW_CAP) m += "cell overflow list full; ";
+      if (h & ERR_NLIST) m += "solute neighbour list: a bead had more than 64 neighbours; ";
       return fail(MPCD_EDEVICE, m);
     }
     return MPCD_OK;
@@ -441,6 +454,7 @@ struct Engine {
     std::vector<int2> sp[NVAR], bst, bt, mt;
     std::vector<ScanSeg> bseg;
     any_beads = false;
+    wca_substeps = 0;
     int max_cl = 1;
     for (Box* b : live)
       if (b->nbead > 0) max_cl = std::max(max_cl, (int)b->p.chain_len);
@@ -464,6 +478,7 @@ struct Engine {
       for (int c0 = 0; c0 < d.ncells; c0 += BLOCK) sp[variant].push_back(make_int2((int)i, c0));
       if (d.nbead > 0) {
         any_beads = true;
+        if (d.wca) wca_substeps = std::max(wca_substeps, (int)d.md_substeps);
         bseg.push_back(ScanSeg{d.bcount, d.bstart, d.nctiles, 0});
         for (int c0 = 0; c0 < d.nctiles; c0 += STILE)
           bst.push_back(make_int2((int)bseg.size() - 1, c0));
@@ -521,6 +536,8 @@ struct Engine {
   // Solute: MD substeps and bead grouping for the step in the records.
   void launch_beads() {
     if (!any_beads) return;
+    if (wca_substeps > 0)
+      launch_wca_md(d_boxes, d_btiles, n_btiles, wca_substeps, d_err, stream);
     launch_md_bin(d_boxes, d_mdtiles, n_mdtiles, md_chains_per_block, md_threads, d_err, stream);
     launch_scan(d_bsegs, d_bstiles, n_bstiles, d_tsum, d_gscan, d_toff, grid_for(n_bstiles, 8),
                 stream);
@@ -747,6 +764,26 @@ struct Engine {
       if ((rc = alloc(b, d.bstart, (size_t)d.nctiles + 1))) return rc;
       CUDA_TRY(cudaMemsetAsync(d.bcount, 0, sizeof(uint32_t) * d.nctiles, stream));
       CUDA_TRY(cudaMemsetAsync(d.bstart, 0, sizeof(uint32_t) * (d.nctiles + 1), stream));
+      if (p.lj_epsilon > 0.0) {  // non-bonded WCA repulsion (Sec. 4.3 reading)
+        const double s2 = p.lj_sigma * p.lj_sigma;
+        const double rcut = std::pow(2.0, 1.0 / 6.0) * p.lj_sigma;
+        d.wca = 1;
+        d.lj_eps = p.lj_epsilon;
+        d.lj_sig2 = s2;
+        d.wca_rc2 = std::pow(2.0, 1.0 / 3.0) * s2;
+        d.wca_rl2 = (rcut + NL_SKIN) * (rcut + NL_SKIN);
+        d.wca_half_skin2 = 0.25 * NL_SKIN * NL_SKIN;
+        d.nl_hsize = (int32_t)(2 * ((nbead + PTILE - 1) / PTILE) * PTILE);
+        if ((rc = alloc(b, d.nl_head, (size_t)d.nl_hsize))) return rc;
+        if ((rc = alloc(b, d.nl_next, (size_t)nbead))) return rc;
+        if ((rc = alloc(b, d.nl_key, (size_t)nbead))) return rc;
+        if ((rc = alloc(b, d.nl_cnt, (size_t)nbead))) return rc;
+        if ((rc = alloc(b, d.nl_nbr, (size_t)nbead * NL_MAX))) return rc;
+        if ((rc = alloc(b, d.nl_rb, (size_t)nbead * 3))) return rc;
+        if ((rc = alloc(b, d.bF, (size_t)nbead * 3))) return rc;
+        if ((rc = alloc(b, d.nl_stale, 1))) return rc;
+        CUDA_TRY(cudaMemsetAsync(d.nl_stale, 0, sizeof(int32_t), stream));
+      }
     }
     d.cur = 0;
     b->nsol = nsol;

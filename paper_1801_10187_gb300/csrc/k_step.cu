@@ -67,8 +67,10 @@ __global__ void k_md_bin(const BoxDev* __restrict__ boxes, const int2* __restric
     }
   }
   __syncthreads();
-  if (active) bond_force(B, sr, j, j % cl, F);
-  for (int s = 0; s < B.md_substeps; ++s) {
+  // boxes with the non-bonded repulsion ran their MD in k_wca.cu; bin only
+  const int nsub = B.wca ? 0 : B.md_substeps;
+  if (active && nsub > 0) bond_force(B, sr, j, j % cl, F);
+  for (int s = 0; s < nsub; ++s) {
     __syncthreads();  // everyone has read sr for the forces
     if (active) {
 #pragma unroll

@@ -12,6 +12,11 @@ namespace mpcd {
 // variant = (thermostat ? 1 : 0) | (solute beads or walls ? 2 : 0) |
 // (Andersen rule ? 16 : 0) | (angular-momentum correction ? 32 : 0); the last
 // two without solute or walls.
+// Solute MD of one collision step for the boxes with the non-bonded WCA
+// repulsion (k_wca.cu): neighbour-list build, then max_substeps velocity-
+// Verlet substeps (each box takes its own md_substeps).
+void launch_wca_md(const BoxDev* boxes, const int2* tiles, int ntiles, int max_substeps, int* err,
+                   cudaStream_t s);
 int cells_blocks_per_sm(bool mixed, int variant, int mode);
 void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const int2* spans,
                   int nspans, int grid, int* err, cudaStream_t s);

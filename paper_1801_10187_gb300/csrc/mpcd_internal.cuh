@@ -42,6 +42,9 @@ constexpr int STILE = 2048;    // entries per scan tile
 constexpr int BLOCK = 256;     // threads per block; the fused step has one thread per cell
 constexpr int BEAD_TILE = 32;  // cells per bead group
 constexpr int ERR_OVERFLOW_CAP = 4;  // overflow list full (cannot happen: it holds N records)
+constexpr int ERR_NLIST = 8;   // solute neighbour list: more than NL_MAX pairs for a bead
+constexpr int NL_MAX = 64;     // neighbours per bead in the solute pair list
+constexpr double NL_SKIN = 0.4;  // neighbour-list buffer (the paper's 0.4 a)
 
 // Passes of the fused step kernel.
 enum { MODE_P = 0, MODE_F = 1, MODE_C = 2 };
@@ -110,7 +113,19 @@ struct BoxDev {
   double sig, sigb;
   float sig_f, sigb_f;
   int32_t angular;      // 1: angular-momentum correction after the collision rule
-  int32_t pad_a;
+  int32_t wca;          // 1: non-bonded WCA repulsion between beads
+  // WCA: epsilon, sigma^2, cutoff^2, list radius^2 (cutoff + buffer), (buffer/2)^2
+  double lj_eps, lj_sig2, wca_rc2, wca_rl2, wca_half_skin2;
+  int32_t nl_hsize;     // hash buckets of the bead grid (2 per bead, tile-rounded)
+  int32_t pad_w;
+  int32_t* nl_head;     // bucket -> first bead (-1 empty)
+  int32_t* nl_next;     // bead -> next bead in its bucket
+  int32_t* nl_key;      // bead -> its cell (edge 1, unshifted) at the build
+  int32_t* nl_cnt;      // bead -> neighbours listed
+  int32_t* nl_nbr;      // bead -> neighbours (NL_MAX each)
+  double* nl_rb;        // positions at the build (3 per bead)
+  double* bF;           // forces on the beads (3 per bead)
+  int32_t* nl_stale;    // 1: a bead moved more than half the buffer since the build
 };
 
 // Segments for the segmented exclusive scan (cells of each box, and bead

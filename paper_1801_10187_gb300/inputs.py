@@ -121,6 +121,14 @@ WORKLOADS = {
                                        steps=500, n_chains=2000, chain_len=50,
                                        bead_mass=5.0, bond_k=1000.0, bond_r0=0.5,
                                        md_substeps=10),
+    # the paper's polymer benchmark (Sec. 4.3): L = 50, 1024 chains of 50 beads
+    # in the density-10 FP64 solvent, velocity Verlet every 0.002 (50 substeps
+    # per collision), non-bonded WCA repulsion (eps = kT, sigma = 0.5)
+    "srd-50c-rho10-fp64-polymer": dict(n=(50, 50, 50), density=10, alpha_deg=130.0, dt=0.1,
+                                       kT=1.0, seed=5, thermostat=False, precision="fp64",
+                                       steps=200, n_chains=1024, chain_len=50, bead_mass=5.0,
+                                       bond_k=1000.0, bond_r0=0.5, md_substeps=50,
+                                       lj_epsilon=1.0, lj_sigma=0.5),
     # 64 boxes of ensemble() stepped together, against the same boxes stepped
     # one after another
     "srd-batch64-mixed": dict(kind="batch", n_boxes=64, ensemble_seed=4, dt=0.1, kT=1.0,
@@ -131,3 +139,65 @@ WORKLOADS = {
                                alpha_deg=130.0, precision="mixed", sweep_rates=(5.0, 10.0, 15.0),
                                sweep_jobs=300),
 }
+
+
+def avoiding_chains(n_cells, n_chains: int, chain_len: int, r0: float, min_dist: float,
+                    kT: float = 1.0, bead_mass: float = 5.0, seed: int = 3):
+    """Random-walk chains (bond length r0) in which no two beads, of the same
+    chain or of different chains, start closer than min_dist (minimum image):
+    an initial state for beads with a non-bonded repulsion.  Each step draws
+    up to 200 directions; a chain that gets stuck restarts elsewhere."""
+    rng = np.random.default_rng(seed)
+    L = np.array([int(x) for x in n_cells], dtype=np.float64)
+    grid = {}
+    placed = []
+
+    def key(p):
+        return tuple(int(x) for x in np.floor(p / 1.0) % L)
+
+    def free(p):
+        k = key(p)
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    kk = ((k[0] + dx) % int(L[0]), (k[1] + dy) % int(L[1]), (k[2] + dz) % int(L[2]))
+                    for q in grid.get(kk, ()):
+                        d = q - p
+                        d -= L * np.rint(d / L)
+                        if d @ d < min_dist * min_dist:
+                            return False
+        return True
+
+    for c in range(n_chains):
+        while True:
+            chain = []
+            p = rng.random(3) * L
+            if not free(p):
+                continue
+            chain.append(p)
+            ok = True
+            for _ in range(chain_len - 1):
+                for _try in range(200):
+                    step = rng.standard_normal(3)
+                    q = np.mod(chain[-1] + r0 * step / np.linalg.norm(step), L)
+                    if free(q) and all(np.sum(((q - x) - L * np.rint((q - x) / L)) ** 2)
+                                       >= min_dist * min_dist for x in chain):
+                        break
+                else:
+                    ok = False
+                    break
+                chain.append(q)
+            if ok:
+                break
+        for p in chain:
+            grid.setdefault(key(p), []).append(p)
+            placed.append(p)
+    pos = np.array(placed).reshape(-1, 3)
+    for k in range(3):
+        over = pos[:, k] >= L[k]
+        pos[over, k] = _below(L[k], np.float64)
+    nb = n_chains * chain_len
+    vel = rng.standard_normal((nb, 3)) * np.sqrt(kT / bead_mass)
+    if nb > 0:
+        vel -= vel.mean(axis=0)
+    return np.ascontiguousarray(pos), np.ascontiguousarray(vel)
