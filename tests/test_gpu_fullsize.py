@@ -137,3 +137,38 @@ def test_fullsize_batch64():
     for n, o, b in zip(counts, ob0, P1):
         bound = steps * 2.0**-24 * math.sqrt(2.0 * n * o["KE"])
         assert np.max(np.abs(o["P"] - b)) <= bound
+
+
+def test_fullsize_polymer_benchmark_conserves():
+    """The paper's polymer benchmark (Sec. 4.3) at full size: 1.25e6 FP64
+    solvent particles and 1024 chains of 50 beads with the WCA repulsion.
+    The oracle's every-pair loop is too slow here, so the test checks what
+    holds at any size: total momentum (collisions and pair forces conserve
+    it) and total energy (SRD collisions conserve kinetic energy; velocity
+    Verlet with h = 0.002 keeps the rest to well below 1e-4)."""
+    cfg = W["srd-50c-rho10-fp64-polymer"]
+    kw = box_kw(cfg)
+    kw.update(lj_epsilon=cfg["lj_epsilon"], lj_sigma=cfg["lj_sigma"])
+    s = inputs.solvent(cfg["n"], cfg["density"], kT=cfg["kT"], seed=cfg["seed"])
+    sp, sv = inputs.avoiding_chains(cfg["n"], cfg["n_chains"], cfg["chain_len"], cfg["bond_r0"],
+                                    0.9 * cfg["lj_sigma"], bead_mass=cfg["bead_mass"],
+                                    seed=cfg["seed"] + 1000)
+    p = oracle_params(kw)
+    p.lj_epsilon, p.lj_sigma = cfg["lj_epsilon"], cfg["lj_sigma"]
+    M = cfg["bead_mass"]
+
+    def totals(vel, spos, svel):
+        P = vel.sum(axis=0) + M * svel.sum(axis=0)
+        E = 0.5 * (vel ** 2).sum() + 0.5 * M * (svel ** 2).sum() + oracle.solute_energy(p, spos)
+        return P, E, np.abs(vel).sum() + M * np.abs(svel).sum()
+
+    P0, E0, scale = totals(s.vel, sp, sv)
+    box = pkg.Box(**kw)
+    box.set_state(s.pos, s.vel, sp, sv)
+    box.step(3)
+    pos, vel, spos, svel, st = box.get_state()
+    box.close()
+    assert st == 3
+    P1, E1, _ = totals(vel, spos, svel)
+    assert np.max(np.abs(P1 - P0)) <= 1e-10 * scale
+    assert abs(E1 - E0) <= 1e-4 * abs(E0)
