@@ -183,14 +183,18 @@ __global__ void __launch_bounds__(WCA_THREADS) k_wca_force(const BoxDev* __restr
 
 // First half of a velocity-Verlet substep: half kick, drift (periodic), and
 // the check whether the list still covers every pair within the cutoff.
+// With close_prev, the closing half kick of the previous substep comes first
+// (the same force, added as a separate step, as the substeps are written).
 __global__ void __launch_bounds__(WCA_THREADS) k_wca_kick_drift(const BoxDev* __restrict__ boxes, const int2* __restrict__ tiles,
-                                 int substep) {
+                                 int substep, int close_prev) {
   for_tile_beads(boxes, tiles, [&](const BoxDev& B, int b) {
     if (substep >= B.md_substeps) return;
     double m2 = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double v = B.svel[3 * b + k] + B.md_hh * B.bF[3 * b + k];
+      double v = B.svel[3 * b + k];
+      if (close_prev) v = v + B.md_hh * B.bF[3 * b + k];
+      v = v + B.md_hh * B.bF[3 * b + k];
       const double r = wrap(B.spos[3 * b + k] + B.md_h * v, B.L[k]);
       B.svel[3 * b + k] = v;
       B.spos[3 * b + k] = r;
@@ -201,10 +205,10 @@ __global__ void __launch_bounds__(WCA_THREADS) k_wca_kick_drift(const BoxDev* __
   });
 }
 
-__global__ void __launch_bounds__(WCA_THREADS) k_wca_kick(const BoxDev* __restrict__ boxes, const int2* __restrict__ tiles,
-                           int substep) {
+// Closing half kick of a box's last substep (its force is the last one computed).
+__global__ void __launch_bounds__(WCA_THREADS) k_wca_kick(const BoxDev* __restrict__ boxes, const int2* __restrict__ tiles) {
   for_tile_beads(boxes, tiles, [&](const BoxDev& B, int b) {
-    if (substep >= B.md_substeps) return;
+    if (B.md_substeps <= 0) return;
 #pragma unroll
     for (int k = 0; k < 3; ++k) B.svel[3 * b + k] = B.svel[3 * b + k] + B.md_hh * B.bF[3 * b + k];
   });
@@ -218,14 +222,17 @@ void launch_wca_md(const BoxDev* boxes, const int2* tiles, int ntiles, int max_s
   k_wca_insert<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, 1);
   k_wca_list<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, 1, err);
   k_wca_force<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, 0);
+  // substep sub: kick-drift (closing substep sub - 1 first), rebuild where
+  // stale, force; the last substep's closing kick is a launch of its own, and
+  // so is that of a box whose md_substeps is below the largest
   for (int sub = 0; sub < max_substeps; ++sub) {
-    k_wca_kick_drift<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, sub);
+    k_wca_kick_drift<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, sub, sub > 0);
     k_wca_clear<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, 0);  // rebuild where stale
     k_wca_insert<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, 0);
     k_wca_list<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, 0, err);
     k_wca_force<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, sub + 1);
-    k_wca_kick<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles, sub);
   }
+  k_wca_kick<<<ntiles * WCA_SPLIT, WCA_THREADS, 0, s>>>(boxes, tiles);
 }
 
 }  // namespace mpcd
