@@ -146,7 +146,8 @@ def avoiding_chains(n_cells, n_chains: int, chain_len: int, r0: float, min_dist:
     """Random-walk chains (bond length r0) in which no two beads, of the same
     chain or of different chains, start closer than min_dist (minimum image):
     an initial state for beads with a non-bonded repulsion.  Each step draws
-    up to 200 directions; a chain that gets stuck restarts elsewhere."""
+    up to 200 directions; a chain that gets stuck restarts elsewhere (at most
+    10^4 times, then ValueError)."""
     rng = np.random.default_rng(seed)
     L = np.array([int(x) for x in n_cells], dtype=np.float64)
     grid = {}
@@ -169,7 +170,7 @@ def avoiding_chains(n_cells, n_chains: int, chain_len: int, r0: float, min_dist:
         return True
 
     for c in range(n_chains):
-        while True:
+        for _restart in range(10000):
             chain = []
             p = rng.random(3) * L
             if not free(p):
@@ -189,6 +190,8 @@ def avoiding_chains(n_cells, n_chains: int, chain_len: int, r0: float, min_dist:
                 chain.append(q)
             if ok:
                 break
+        else:
+            raise ValueError("avoiding_chains: no room for another chain at this min_dist")
         for p in chain:
             grid.setdefault(key(p), []).append(p)
             placed.append(p)
