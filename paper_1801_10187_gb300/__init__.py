@@ -112,6 +112,8 @@ def lib():
     L.mpcd_box_footprint.restype = i64
     L.mpcd_batch_add.argtypes = [vp, P(_Params), i64, dp, dp, u64, P(i32)]
     L.mpcd_batch_step.argtypes = [vp, i64]
+    L.mpcd_tune.argtypes = [vp, i64, P(i32), dp, P(i64)]
+    L.mpcd_batch_tune.argtypes = [vp, i64, P(i32), dp, P(i64)]
     L.mpcd_batch_get_state.argtypes = [vp, i32, dp, dp, P(u64)]
     L.mpcd_batch_observables.argtypes = [vp, i32, P(_Obs)]
     L.mpcd_batch_remove.argtypes = [vp, i32]
@@ -124,7 +126,7 @@ def lib():
                  "mpcd_get_state", "mpcd_get_state_device", "mpcd_observables", "mpcd_profile",
                  "mpcd_last_cells", "mpcd_phase_times", "mpcd_profile_noalloc", "mpcd_batch_create", "mpcd_batch_add", "mpcd_batch_step",
                  "mpcd_batch_get_state", "mpcd_batch_observables", "mpcd_batch_remove",
-                 "mpcd_batch_info", "mpcd_batch_sync"):
+                 "mpcd_batch_info", "mpcd_batch_sync", "mpcd_tune", "mpcd_batch_tune"):
         getattr(L, name).restype = c_int
     _lib_handle = L
     return L
@@ -173,6 +175,13 @@ def make_params(n=(10, 10, 10), dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=
     p.lj_epsilon = float(lj_epsilon)
     p.lj_sigma = float(lj_sigma)
     return p
+
+
+def _tune(fn, handle, steps_per_candidate):
+    bps, ms, taken = ctypes.c_int32(0), ctypes.c_double(0.0), ctypes.c_int64(0)
+    _check(fn(handle, int(steps_per_candidate), ctypes.byref(bps), ctypes.byref(ms),
+              ctypes.byref(taken)))
+    return bps.value, ms.value, taken.value
 
 
 def _obs_dict(o: _Obs) -> dict:
@@ -231,6 +240,11 @@ class Box:
 
     def step(self, nsteps=1):
         _check(lib().mpcd_step(self._ctx, int(nsteps)))
+
+    def tune(self, steps_per_candidate=2):
+        """Launch tuner (mpcd_tune): returns (blocks per SM or -1, ms per
+        step of the choice, steps the simulation advanced)."""
+        return _tune(lib().mpcd_tune, self._ctx, steps_per_candidate)
 
     def get_state(self):
         pos = np.empty((self.n_solvent, 3))
@@ -328,6 +342,10 @@ class Batch:
 
     def step(self, nsteps=1):
         _check(lib().mpcd_batch_step(self._b, int(nsteps)))
+
+    def tune(self, steps_per_candidate=2):
+        """mpcd_batch_tune: (blocks per SM or -1, ms per step, steps taken)."""
+        return _tune(lib().mpcd_batch_tune, self._b, steps_per_candidate)
 
     def get_state(self, slot: int):
         n = self.sizes[slot]

@@ -517,10 +517,20 @@ struct Engine {
     return n < g ? std::max(n, 1) : g;
   }
 
+  // Grid of the fused pass: tuned_grid 0 = the occupancy limit (blocks per
+  // SM that fit), k > 0 = at most k blocks per SM, -1 = one block per span.
+  int tuned_grid = 0;
+  int grid_of(int v, int mode) const {
+    if (mode == MODE_F && tuned_grid == -1) return std::max(n_spans[v], 1);
+    const int bps = (mode == MODE_F && tuned_grid > 0) ? std::min(tuned_grid, cells_bps[mode][v])
+                                                      : cells_bps[mode][v];
+    return grid_for(n_spans[v], bps);
+  }
+
   void launch_cells_all(int mode) {
     for (int v = 0; v < NVAR; ++v) {
       if (n_spans[v] == 0) continue;
-      const int grid = grid_for(n_spans[v], cells_bps[mode][v]);
+      const int grid = grid_of(v, mode);
       const bool at = (v & 16) != 0;
       if ((v & 4) && mixed)
         launch_cells_warp((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, (v & 32) != 0, mode,
@@ -604,6 +614,62 @@ struct Engine {
     }
     CUDA_TRY(cudaGetLastError());
     return MPCD_OK;
+  }
+
+  // Launch tuner.  The paper tunes its kernels' launch parameters at run time
+  // on real steps (Sec. 3.5, Sec. 4).  Here each candidate grid of the fused
+  // pass (1 .. occupancy-limit blocks per SM, and one block per span) runs
+  // `reps` real steps, timed with CUDA events on the stream; the fastest is
+  // kept and the step graph re-captured.  Results do not depend on the grid:
+  // the mixed model's cell sums are exact, the FP64 ones differ at rounding.
+  int tune(int64_t reps, int32_t* chosen, double* best_ms, int64_t* steps_taken) {
+    if (reps < 1) return fail(MPCD_EINVAL, "steps per candidate < 1");
+    int rc = ensure_tables();
+    if (rc) return rc;
+    int64_t taken = 0;
+    if (live.empty()) {
+      if (steps_taken) *steps_taken = 0;
+      return MPCD_OK;
+    }
+    if (!pending) {
+      if ((rc = run_pass(MODE_P))) return rc;
+      pending = true;
+      taken += 1;
+    }
+    int maxbps = 1;
+    for (int v = 0; v < NVAR; ++v)
+      if (n_spans[v] > 0) maxbps = std::max(maxbps, cells_bps[MODE_F][v]);
+    std::vector<int> cand;
+    for (int k = 1; k <= maxbps; ++k) cand.push_back(k);
+    cand.push_back(-1);
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e30;
+    int best_c = 0;
+    for (int c : cand) {
+      tuned_grid = c;
+      CUDA_TRY(cudaEventRecord(e0, stream));
+      for (int64_t r = 0; r < reps; ++r) enqueue_pass(MODE_F);
+      CUDA_TRY(cudaEventRecord(e1, stream));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      taken += reps;
+      if (ms / (double)reps < best) {
+        best = ms / (double)reps;
+        best_c = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tuned_grid = best_c;
+    drop_graphs();
+    CUDA_TRY(cudaGetLastError());
+    if (chosen) *chosen = best_c;
+    if (best_ms) *best_ms = best;
+    if (steps_taken) *steps_taken = taken;
+    return check_err();
   }
 
   // Finish the pending collision so the records hold a completed step.
@@ -1029,6 +1095,14 @@ int mpcd_step(mpcd_ctx* ctx, int64_t nsteps) {
   return ctx->eng.step(nsteps);
 }
 
+int mpcd_tune(mpcd_ctx* ctx, int64_t steps_per_candidate, int32_t* blocks_per_sm,
+              double* ms_per_step, int64_t* steps_taken) {
+  g_last_error.clear();
+  if (!ctx) return fail(MPCD_EINVAL, "ctx is NULL");
+  if (!ctx->box->has_state) return fail(MPCD_ESTATE, "no state set");
+  return ctx->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken);
+}
+
 int mpcd_get_state(mpcd_ctx* ctx, double* pos, double* vel, double* solute_pos, double* solute_vel,
                    uint64_t* step) {
   g_last_error.clear();
@@ -1250,6 +1324,13 @@ int mpcd_batch_step(mpcd_batch* bt, int64_t nsteps) {
   g_last_error.clear();
   if (!bt) return fail(MPCD_EINVAL, "batch is NULL");
   return bt->eng.step(nsteps);
+}
+
+int mpcd_batch_tune(mpcd_batch* bt, int64_t steps_per_candidate, int32_t* blocks_per_sm,
+                    double* ms_per_step, int64_t* steps_taken) {
+  g_last_error.clear();
+  if (!bt) return fail(MPCD_EINVAL, "batch is NULL");
+  return bt->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken);
 }
 
 int mpcd_batch_get_state(mpcd_batch* bt, int32_t slot, double* pos, double* vel, uint64_t* step) {

@@ -346,3 +346,25 @@ def test_mixed_row_capacity_limits(rho):
     np.testing.assert_array_equal(counts, rk)
     np.testing.assert_array_equal(pos, ref.pos)
     np.testing.assert_array_equal(vel, ref.vel)
+
+
+def test_launch_tuner_keeps_results():
+    """mpcd_tune runs real steps under each candidate grid and keeps the
+    fastest; the trajectory is bit-identical to plain steps (mixed model)."""
+    s = inputs.solvent((24, 24, 24), 10, seed=51, mixed=True)
+    a = pkg.Box(n=(24, 24, 24), seed=51, precision="mixed", thermostat=True)
+    a.set_state(s.pos, s.vel)
+    bps, ms, taken = a.tune(1)
+    assert bps == -1 or bps >= 1
+    assert ms > 0.0 and taken >= 2
+    a.step(3)
+    pa, va, *_, sta = a.get_state()
+    a.close()
+    b = pkg.Box(n=(24, 24, 24), seed=51, precision="mixed", thermostat=True)
+    b.set_state(s.pos, s.vel)
+    b.step(taken + 3)
+    pb, vb, *_, stb = b.get_state()
+    b.close()
+    assert sta == stb == taken + 3
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(va, vb)
