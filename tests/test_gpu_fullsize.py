@@ -3,14 +3,16 @@ configuration the benchmark times (captured graphs of the fused pass, one
 launch per step), against the oracle run on the same states.
 
   * 100^3 cells at density 10 (10^7 particles), mixed and FP64, and the
-    Andersen-rule variant of the mixed box: two steps (the stream/bin pass,
-    one fused collide + stream/bin pass, and the completing collision), every
-    particle compared.
+    Andersen-rule and angular-correction variants of the mixed box: two steps
+    (the stream/bin pass, one fused collide + stream/bin pass, and the
+    completing collision), every particle compared.
   * 250^3 cells at density 5 (7.8 * 10^7 particles) with 2000 chains of 50
     beads and the cell thermostat: two steps, every particle compared.
   * the 64-box ensemble (about 1.5 * 10^8 particles) stepped in one batch:
     three boxes compared particle by particle, and for every box the
     momentum conservation that holds at any size.
+  * the paper's polymer benchmark (1.25e6 FP64 solvent particles, 1024 chains
+    of 50 repelling beads): total momentum and energy conserved.
 Tolerances as in the small parity tests: mixed bit-exact, FP64 1e-12
 relative per step.  These runs take a few minutes of oracle time.
 """
