@@ -77,6 +77,7 @@ struct SpanParams {
   double dt, ca, sa, omc, m, Mb;
   double L[3], hg[3], gdt[3];
   long long S[3];  // grid shift of the step the records are binned for
+  double s[3];     // the same as doubles (S 2^-32, exact)
   int n[3], K;
   RecD* rows_cur;
   RecD* rows_out;
@@ -130,7 +131,10 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
         P.ovf_cell_out = B.ovf_cell[out];
         P.ovf_n_out = &B.ovf_n[out];
         P.ovf_cap = B.ovf_cap;
-        if (MODE != MODE_C) shift_units(B, MODE == MODE_P ? t : t + 1ull, P.S);
+        if (MODE != MODE_C) {
+          shift_units(B, MODE == MODE_P ? t : t + 1ull, P.S);
+          for (int q = 0; q < 3; ++q) P.s[q] = (double)P.S[q] * 0x1p-32;
+        }
       }
       __syncthreads();
       box_of_params = tt.x;
@@ -460,11 +464,10 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
           r[q] = fma(w[q], H.dt, r[q]) + H.hg[q];
           w[q] = w[q] + H.gdt[q];
         } else {
-          r[q] = fma(w[q], H.dt, r[q]) + 0.0;
-          w[q] = w[q] + 0.0;
+          r[q] = fma(w[q], H.dt, r[q]);  // FP64 parity is to rounding: no -0 -> +0 step
         }
-        r[q] = wrap(r[q], H.L[q]);
-        int i = axis_cell(r[q], H.S[q]);
+        r[q] = wrap(r[q], H.L[q]);  // finite, in [0, L)
+        int i = (int)floor(r[q] - H.s[q]);  // in [-1, n]: floor(x - s) exactly (Sec. 3.4)
         if (i < 0) i += H.n[q];
         if (i >= H.n[q]) i -= H.n[q];
         if (i < 0 || i >= H.n[q]) {
