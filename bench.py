@@ -39,7 +39,10 @@ from paper_1801_10187_gb300 import inputs  # noqa: E402
 
 FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 (non-tensor) rate
-FP64_FLOPS_PER_PARTICLE = 66     # algorithmic FP64 flops per particle-step
+# FP64 flops per particle-step of the collide + stream/bin pass (FMA = 2, no
+# compares): cell sum 3, v - u 3, rotation about the cell axis 30, u + R d 3,
+# r + v dt 6, r - s 3.  The per-cell work (u, the axis) is not counted.
+FP64_FLOPS_PER_PARTICLE = 48
 METRIC = "MPCD particle-steps/s"
 UNIT = "particle-steps/s"
 # kernels launched per step: the fused cell kernel and the record update; the

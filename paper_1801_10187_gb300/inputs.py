@@ -129,6 +129,13 @@ WORKLOADS = {
                                        steps=200, n_chains=1024, chain_len=50, bead_mass=5.0,
                                        bond_k=1000.0, bond_r0=0.5, md_substeps=50,
                                        lj_epsilon=1.0, lj_sigma=0.5),
+    # the solute + thermostat workload at 1/16 of its volume (5 * 10^6 particles,
+    # 128 chains): the same kernels on a state small enough to profile in full
+    "srd-100c-rho5-mixed-solute": dict(n=(100, 100, 100), density=5, alpha_deg=130.0, dt=0.1,
+                                       kT=1.0, seed=3, thermostat=True, precision="mixed",
+                                       steps=500, n_chains=128, chain_len=50,
+                                       bead_mass=5.0, bond_k=1000.0, bond_r0=0.5,
+                                       md_substeps=10),
     # 64 boxes of ensemble() stepped together, against the same boxes stepped
     # one after another
     "srd-batch64-mixed": dict(kind="batch", n_boxes=64, ensemble_seed=4, dt=0.1, kT=1.0,
