@@ -455,10 +455,16 @@ struct Engine {
     std::vector<ScanSeg> bseg;
     any_beads = false;
     wca_substeps = 0;
-    int max_cl = 1;
+    int max_cl = 1, total_chains = 0;
     for (Box* b : live)
-      if (b->nbead > 0) max_cl = std::max(max_cl, (int)b->p.chain_len);
-    md_chains_per_block = std::max(1, BLOCK / max_cl);
+      if (b->nbead > 0) {
+        max_cl = std::max(max_cl, (int)b->p.chain_len);
+        total_chains += (int)(b->nbead / b->p.chain_len);
+      }
+    // A block runs its chains' substeps one after another on the FP64 pipe of
+    // one SM: with few chains, put fewer in each block so that they spread
+    // over the SMs (two blocks per SM before a block takes a second chain).
+    md_chains_per_block = std::max(1, std::min(BLOCK / max_cl, total_chains / (2 * nsm)));
     md_threads = ((md_chains_per_block * max_cl + 31) / 32) * 32;
     for (size_t i = 0; i < live.size(); ++i) {
       Box* b = live[i];

@@ -16,39 +16,54 @@ namespace mpcd {
 // Solute: velocity-Verlet substeps with harmonic bonds along each chain, then
 // binning of the beads with the step's shift.  One block holds whole chains
 // in shared memory; bead j of the block is thread j.
+//
+// Each bond's force is computed once, by the bead at its left end, as
+// g = f d with d = r_{j+1} - r_j; the bead at its right end adds -g.  That is
+// the same value, bit for bit, as computing the bond from its own side:
+// the difference, the minimum image (rint is odd), the norm and f * d are all
+// odd or even in d exactly, so each bead's force is 0 + (left) + (right) as
+// before, with one square root and one division per bond instead of two.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void bond_force(const BoxDev& B, const double* __restrict__ sr, int j,
-                                           int pos_in_chain, double F[3]) {
+__device__ __forceinline__ void bond_right(const BoxDev& B, const double* __restrict__ sr, int j,
+                                           int pos_in_chain, double* __restrict__ sg,
+                                           int* __restrict__ sok) {
+  if (pos_in_chain == B.chain_len - 1) return;  // the chain's last bead: no bond on its right
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    d[k] = sr[3 * (j + 1) + k] - sr[3 * j + k];
+    // minimum image; a bond shorter than L/4 needs no image (rint gives 0),
+    // which saves the FP64 division on nearly every bond
+    if (!(fabs(d[k]) < 0.25 * B.L[k])) d[k] = d[k] - B.L[k] * rint(d[k] / B.L[k]);
+  }
+  const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  const bool ok = dist > 0.0;  // coincident beads: no force
+  sok[j] = ok ? 1 : 0;
+  if (!ok) return;
+  const double f = (B.bond_k * (dist - B.bond_r0)) / dist;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sg[3 * j + k] = f * d[k];
+}
+
+__device__ __forceinline__ void bond_force(const BoxDev& B, const double* __restrict__ sg,
+                                           const int* __restrict__ sok, int j, int pos_in_chain,
+                                           double F[3]) {
   F[0] = F[1] = F[2] = 0.0;
+  if (pos_in_chain > 0 && sok[j - 1]) {
 #pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    int o;
-    if (side == 0) {
-      if (pos_in_chain == 0) continue;
-      o = j - 1;
-    } else {
-      if (pos_in_chain == B.chain_len - 1) continue;
-      o = j + 1;
-    }
-    double d[3];
+    for (int k = 0; k < 3; ++k) F[k] += -sg[3 * (j - 1) + k];
+  }
+  if (pos_in_chain < B.chain_len - 1 && sok[j]) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      d[k] = sr[3 * o + k] - sr[3 * j + k];
-      // minimum image; a bond shorter than L/4 needs no image (rint gives 0),
-      // which saves the FP64 division on nearly every bond
-      if (!(fabs(d[k]) < 0.25 * B.L[k])) d[k] = d[k] - B.L[k] * rint(d[k] / B.L[k]);
-    }
-    const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    if (!(dist > 0.0)) continue;
-    const double f = (B.bond_k * (dist - B.bond_r0)) / dist;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) F[k] += f * d[k];
+    for (int k = 0; k < 3; ++k) F[k] += sg[3 * j + k];
   }
 }
 
 __global__ void k_md_bin(const BoxDev* __restrict__ boxes, const int2* __restrict__ tiles,
                          int chains_per_block, int* err) {
-  extern __shared__ double sr[];  // 3 * beads of this block
+  extern __shared__ double sr[];  // 3 * beads of this block, then the bond forces, then flags
+  double* sg = sr + 3 * blockDim.x;
+  int* sok = reinterpret_cast<int*>(sg + 3 * blockDim.x);
   const int2 tt = tiles[blockIdx.x];
   const BoxDev& B = boxes[tt.x];
   const int cl = B.chain_len;
@@ -56,6 +71,7 @@ __global__ void k_md_bin(const BoxDev* __restrict__ boxes, const int2* __restric
   const int nbb = nchains * cl;
   const int j = threadIdx.x;
   const bool active = j < nbb;
+  const int pos = j % cl;
   const int b = tt.y * cl + j;
   double r[3] = {0, 0, 0}, v[3] = {0, 0, 0}, F[3];
   if (active) {
@@ -66,12 +82,17 @@ __global__ void k_md_bin(const BoxDev* __restrict__ boxes, const int2* __restric
       sr[3 * j + k] = r[k];
     }
   }
-  __syncthreads();
   // boxes with the non-bonded repulsion ran their MD in k_wca.cu; bin only
   const int nsub = B.wca ? 0 : B.md_substeps;
-  if (active && nsub > 0) bond_force(B, sr, j, j % cl, F);
+  if (nsub > 0) {
+    __syncthreads();
+    if (active) bond_right(B, sr, j, pos, sg, sok);
+    __syncthreads();
+    if (active) bond_force(B, sg, sok, j, pos, F);
+  }
   for (int s = 0; s < nsub; ++s) {
-    __syncthreads();  // everyone has read sr for the forces
+    // every read of sr (the bonds) and of sg (the forces) of the last phase
+    // came before a barrier that this thread has passed
     if (active) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -81,8 +102,10 @@ __global__ void k_md_bin(const BoxDev* __restrict__ boxes, const int2* __restric
       }
     }
     __syncthreads();
+    if (active) bond_right(B, sr, j, pos, sg, sok);
+    __syncthreads();
     if (active) {
-      bond_force(B, sr, j, j % cl, F);
+      bond_force(B, sg, sok, j, pos, F);
 #pragma unroll
       for (int k = 0; k < 3; ++k) v[k] = v[k] + B.md_hh * F[k];
     }
@@ -268,7 +291,7 @@ __global__ void k_after_pass(BoxDev* boxes, int nboxes, int flip, int advance) {
 void launch_md_bin(const BoxDev* boxes, const int2* tiles, int ntiles, int chains_per_block,
                    int threads, int* err, cudaStream_t s) {
   if (ntiles <= 0) return;
-  const size_t sm = sizeof(double) * 3 * (size_t)threads;
+  const size_t sm = (sizeof(double) * 6 + sizeof(int)) * (size_t)threads;
   k_md_bin<<<ntiles, threads, sm, s>>>(boxes, tiles, chains_per_block, err);
 }
 

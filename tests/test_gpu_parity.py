@@ -226,6 +226,35 @@ def test_solute_chains(precision):
     assert np.max(np.abs(spos - ref.spos)) <= 1e-11
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solute_many_chains_over_blocks(precision):
+    # 701 chains of 10 beads: two chains per MD block, the last block with
+    # one; every bond force is computed once and shared by its two beads
+    n = (20, 20, 20)
+    s = inputs.solvent(n, 5, seed=41, mixed=precision == "mixed")
+    sp, sv = inputs.chains(n, 701, 10, 0.5, bead_mass=5.0, seed=42)
+    kw = dict(chain_len=10, md_substeps=10, solute_mass=5.0, bond_k=1000.0, bond_r0=0.5)
+    box = pkg.Box(n=n, seed=41, precision=precision, **kw)
+    box.set_state(s.pos, s.vel, sp, sv)
+    box.step(2)
+    pos, vel, spos, svel, st = box.get_state()
+    cells, counts = box.last_cells()
+    box.close()
+    p = oracle.Params(n=n, seed=41, precision=oracle.MIXED if precision == "mixed" else oracle.FP64,
+                      **kw)
+    ref = oracle.State(s.pos.copy(), s.vel.copy(), sp.copy(), sv.copy())
+    rc, rk = oracle.step(p, ref, 2, want_cells=True)
+    assert np.array_equal(cells, rc)
+    assert np.array_equal(counts, rk)
+    if precision == "mixed":
+        assert np.array_equal(vel, ref.vel)
+        assert rel_err(svel, ref.svel, m=5.0) == 0.0
+    else:
+        assert rel_err(vel, ref.vel) <= 2e-11
+        assert rel_err(svel, ref.svel, m=5.0) <= 2e-11
+    assert np.max(np.abs(spos - ref.spos)) <= 1e-11
+
+
 def test_observables_match_oracle():
     s = inputs.solvent((10, 10, 10), 10, seed=6)
     box = pkg.Box(n=(10, 10, 10), seed=6, precision="fp64", thermostat=True)
