@@ -338,6 +338,7 @@ struct Engine {
           cells_bps[m][v] = 1;
         if (cells_bps[m][v] < 1) cells_bps[m][v] = 1;
       }
+    CUDA_TRY((cudaError_t)md_bin_prepare());
     CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
     CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
     CUDA_TRY(cudaMalloc(&d_partials, sizeof(double) * 4 * 4096));

@@ -288,10 +288,20 @@ __global__ void k_after_pass(BoxDev* boxes, int nboxes, int flip, int advance) {
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
+// Shared memory of k_md_bin: positions and bond forces (3 doubles each) and
+// one flag per thread; 1024 threads (one chain of the longest length) need
+// 53,248 bytes, beyond the 48 KB granted without asking.
+static size_t md_bin_smem(int threads) { return (sizeof(double) * 6 + sizeof(int)) * (size_t)threads; }
+
+int md_bin_prepare() {
+  return (int)cudaFuncSetAttribute(k_md_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)md_bin_smem(1024));
+}
+
 void launch_md_bin(const BoxDev* boxes, const int2* tiles, int ntiles, int chains_per_block,
                    int threads, int* err, cudaStream_t s) {
   if (ntiles <= 0) return;
-  const size_t sm = (sizeof(double) * 6 + sizeof(int)) * (size_t)threads;
+  const size_t sm = md_bin_smem(threads);
   k_md_bin<<<ntiles, threads, sm, s>>>(boxes, tiles, chains_per_block, err);
 }
 

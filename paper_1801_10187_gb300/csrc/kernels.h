@@ -49,6 +49,8 @@ void launch_init_thermal(bool mixed, int n, uint64_t seed, const double L[3], do
                          void* pos, void* vel, unsigned long long* sums, cudaStream_t s);
 
 // ---- solute and pass bookkeeping (k_step.cu) ----
+// Allows k_md_bin the shared memory of 1024-thread blocks; returns a cudaError_t.
+int md_bin_prepare();
 void launch_md_bin(const BoxDev* boxes, const int2* tiles, int ntiles, int chains_per_block,
                    int threads, int* err, cudaStream_t s);
 void launch_scan(const ScanSeg* segs, const int2* tiles, int ntiles, uint32_t* tsum,

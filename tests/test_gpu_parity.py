@@ -255,6 +255,26 @@ def test_solute_many_chains_over_blocks(precision):
     assert np.max(np.abs(spos - ref.spos)) <= 1e-11
 
 
+def test_solute_longest_chain():
+    # one chain of 1024 beads, the longest allowed: one block of 1024 threads
+    # whose positions, bond forces and flags take 53,248 bytes of shared memory
+    n = (12, 12, 12)
+    s = inputs.solvent(n, 5, seed=43, mixed=True)
+    sp, sv = inputs.chains(n, 1, 1024, 0.5, bead_mass=5.0, seed=44)
+    kw = dict(chain_len=1024, md_substeps=5, solute_mass=5.0, bond_k=1000.0, bond_r0=0.5)
+    box = pkg.Box(n=n, seed=43, precision="mixed", **kw)
+    box.set_state(s.pos, s.vel, sp, sv)
+    box.step(2)
+    pos, vel, spos, svel, st = box.get_state()
+    box.close()
+    p = oracle.Params(n=n, seed=43, precision=oracle.MIXED, **kw)
+    ref = oracle.State(s.pos.copy(), s.vel.copy(), sp.copy(), sv.copy())
+    oracle.step(p, ref, 2)
+    assert np.array_equal(vel, ref.vel)
+    assert rel_err(svel, ref.svel, m=5.0) == 0.0
+    assert np.max(np.abs(spos - ref.spos)) <= 1e-11
+
+
 def test_observables_match_oracle():
     s = inputs.solvent((10, 10, 10), 10, seed=6)
     box = pkg.Box(n=(10, 10, 10), seed=6, precision="fp64", thermostat=True)
