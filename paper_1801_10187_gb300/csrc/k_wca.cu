@@ -153,32 +153,145 @@ __global__ void __launch_bounds__(WCA_THREADS) k_wca_list(const BoxDev* __restri
 }
 
 // Bond forces plus the WCA repulsion over the bead's list (Sec. 4.3 reading).
+//
+// The arithmetic is FP64, which issues one warp instruction per many cycles
+// on this GPU, so the kernel keeps the lanes busy rather than the threads
+// few.  A warp owns 32 consecutive beads.  Each lane takes its own bead's two
+// bonds.  The warp's listed pairs are then taken as one flat sequence (bead
+// by bead, in list order), 32 at a time: each lane forms the distance of one
+// pair, and the pairs within the cutoff go, in order, to a queue in shared
+// memory.  Whenever the queue holds 32 pairs, every lane takes one and
+// computes its force; the forces of each bead's run in the queue are added
+// in queue order by the run's first lane.  So the divisions run on full
+// warps however the list lengths and hits are spread over the beads, and the
+// sum is the same on every run.
+namespace {
+constexpr int FW = WCA_THREADS / 32;  // warps per block
+constexpr int QCAP = 64;              // queue: fewer than 32 waiting plus one round of 32
+
+struct ForceWarp {
+  int off[33];          // first flat pair index of each bead; off[32] = all pairs
+  int qown[QCAP];       // queued pair: the warp-local bead it acts on
+  double qd[4][QCAP];   // queued pair: d (3) and r^2
+  double c[3][32];      // forces of one flush, one per lane
+  double F[3][32];      // sum of each bead's pair forces
+  double rb[3][32];     // bead positions
+};
+
+// Forces of queue entries [0, nq): lane l takes entry l; each run of
+// entries of one bead is summed, in order, by its first lane.
+__device__ __forceinline__ void wca_flush(const BoxDev& B, ForceWarp& W, int nq, int lane) {
+  if (lane < nq) {
+    const double r2 = W.qd[3][lane];
+    const double inv = 1.0 / r2;
+    const double x = B.lj_sig2 * inv;
+    const double x6 = x * x * x;
+    const double g = 24.0 * B.lj_eps * x6 * (2.0 * x6 - 1.0) * inv;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) W.c[q][lane] = -(g * W.qd[q][lane]);
+  }
+  __syncwarp();
+  if (lane < nq) {
+    const int own = W.qown[lane];
+    if (lane == 0 || W.qown[lane - 1] != own) {
+      double acc[3] = {W.c[0][lane], W.c[1][lane], W.c[2][lane]};
+      for (int l = lane + 1; l < nq && W.qown[l] == own; ++l) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc[q] += W.c[q][l];
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) W.F[q][own] += acc[q];
+    }
+  }
+  __syncwarp();
+}
+}  // namespace
+
 __global__ void __launch_bounds__(WCA_THREADS) k_wca_force(const BoxDev* __restrict__ boxes, const int2* __restrict__ tiles,
                             int substep) {
-  for_tile_beads(boxes, tiles, [&](const BoxDev& B, int b) {
-    if (substep > B.md_substeps) return;
+  __shared__ ForceWarp fw[FW];
+  const int2 tt = tiles[blockIdx.x / WCA_SPLIT];
+  const BoxDev& B = boxes[tt.x];
+  if (!B.wca || substep > B.md_substeps) return;  // the same for the whole block
+  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  ForceWarp& W = fw[warp];
+  const int b0 = tt.y + (int)(blockIdx.x % WCA_SPLIT) * WCA_THREADS + warp * 32;
+  const int b = b0 + lane;
+  const bool valid = b < B.nbead;
+  double F[3] = {0.0, 0.0, 0.0};
+  int cnt = 0;
+  if (valid) {
     if (b == 0) *B.nl_stale = 0;  // this substep's list kernels have all run
-    double F[3];
     bonds_on(B, b, F);
-    const double rb[3] = {B.spos[3 * b], B.spos[3 * b + 1], B.spos[3 * b + 2]};
-    const int cnt = B.nl_cnt[b];
-    for (int i = 0; i < cnt; ++i) {
-      const int j = B.nl_nbr[(size_t)b * NL_MAX + i];
-      double d[3];
+    cnt = B.nl_cnt[b];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) d[q] = min_image(B.spos[3 * j + q] - rb[q], B.L[q]);
-      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      if (!(r2 < B.wca_rc2)) continue;
-      const double inv = 1.0 / r2;
-      const double x = B.lj_sig2 * inv;
-      const double x6 = x * x * x;
-      const double g = 24.0 * B.lj_eps * x6 * (2.0 * x6 - 1.0) * inv;
+    for (int q = 0; q < 3; ++q) W.rb[q][lane] = B.spos[3 * b + q];
+  }
 #pragma unroll
-      for (int q = 0; q < 3; ++q) F[q] -= g * d[q];
+  for (int q = 0; q < 3; ++q) W.F[q][lane] = 0.0;
+  // flat pair offsets: exclusive scan of the list lengths over the warp
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  W.off[lane] = incl - cnt;
+  if (lane == 31) W.off[32] = incl;
+  __syncwarp();
+  const int total = W.off[32];  // at most 32 NL_MAX
+  int nq = 0;                   // queued pairs (the same in every lane)
+  for (int base = 0; base < total; base += 32) {
+    const int k = base + lane;
+    bool hit = false;
+    int own = 0;
+    double d[3] = {0.0, 0.0, 0.0}, r2 = 0.0;
+    if (k < total) {
+      // the bead of pair k: the last with off <= k (offsets do not decrease)
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (W.off[own + step] <= k) own += step;
+      const int j = B.nl_nbr[(size_t)(b0 + own) * NL_MAX + (k - W.off[own])];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) d[q] = min_image(B.spos[3 * j + q] - W.rb[q][own], B.L[q]);
+      r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      hit = r2 < B.wca_rc2;
     }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, hit);
+    if (hit) {
+      const int pos = nq + __popc(m & ((1u << lane) - 1u));  // < nq + 32 <= QCAP
+      W.qown[pos] = own;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) B.bF[3 * b + q] = F[q];
-  });
+      for (int q = 0; q < 3; ++q) W.qd[q][pos] = d[q];
+      W.qd[3][pos] = r2;
+    }
+    nq += __popc(m);
+    __syncwarp();
+    if (nq >= 32) {
+      wca_flush(B, W, 32, lane);
+      nq -= 32;
+      // move the rest (fewer than 32) to the front
+      int own2 = 0;
+      double e[4] = {0.0, 0.0, 0.0, 0.0};
+      if (lane < nq) {
+        own2 = W.qown[32 + lane];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) e[q] = W.qd[q][32 + lane];
+      }
+      __syncwarp();
+      if (lane < nq) {
+        W.qown[lane] = own2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) W.qd[q][lane] = e[q];
+      }
+      __syncwarp();
+    }
+  }
+  if (nq > 0) wca_flush(B, W, nq, lane);
+  if (valid) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) B.bF[3 * b + q] = F[q] + W.F[q][lane];
+  }
 }
 
 // First half of a velocity-Verlet substep: half kick, drift (periodic), and
