@@ -154,17 +154,19 @@ __global__ void __launch_bounds__(WCA_THREADS) k_wca_list(const BoxDev* __restri
 
 // Bond forces plus the WCA repulsion over the bead's list (Sec. 4.3 reading).
 //
-// The arithmetic is FP64, which issues one warp instruction per many cycles
-// on this GPU, so the kernel keeps the lanes busy rather than the threads
-// few.  A warp owns 32 consecutive beads.  Each lane takes its own bead's two
-// bonds.  The warp's listed pairs are then taken as one flat sequence (bead
-// by bead, in list order), 32 at a time: each lane forms the distance of one
-// pair, and the pairs within the cutoff go, in order, to a queue in shared
-// memory.  Whenever the queue holds 32 pairs, every lane takes one and
-// computes its force; the forces of each bead's run in the queue are added
-// in queue order by the run's first lane.  So the divisions run on full
-// warps however the list lengths and hits are spread over the beads, and the
-// sum is the same on every run.
+// The arithmetic is FP64, and the FP64 pipe issues a warp instruction only
+// every many cycles on this GPU, so what counts is how many lanes of each
+// instruction do useful work.  A warp owns 32 consecutive beads.  Each lane
+// takes its own bead's two bonds.  The warp's listed pairs are then taken as
+// one flat sequence (bead by bead, in list order), 32 at a time: each lane
+// forms the distance of one pair, and the pairs within the cutoff go, in
+// order, to a queue in shared memory.  Whenever the queue holds 32 pairs,
+// every lane takes one and computes its force; the forces of each bead's run
+// in the queue are added in queue order by the run's first lane (no
+// atomics).  So the divisions run on full warps however the list lengths and
+// hits are spread over the beads.  The list order follows the hash grid's
+// insertion order, which may differ between runs, and so may the last bits
+// of a sum.
 namespace {
 constexpr int FW = WCA_THREADS / 32;  // warps per block
 constexpr int QCAP = 64;              // queue: fewer than 32 waiting plus one round of 32
