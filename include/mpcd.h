@@ -116,7 +116,10 @@ typedef struct {
  * (buffer 0.4) is built every collision step and rebuilt within it as soon as
  * a bead has moved more than half the buffer; a bead with more than 64
  * neighbours is reported as MPCD_EDEVICE.  Needs n_k >= 3 and
- * 2^(1/6) sigma + 0.4 <= 1 (EINVAL). */
+ * 2^(1/6) sigma + 0.4 <= 1 (EINVAL).  The list is built through a hash grid
+ * filled by atomic exchange, so the order in which a bead's pair forces are
+ * added, and with it the last bits of the bead states, may differ between
+ * runs; without the repulsion the mixed model is reproducible bit for bit. */
 
 /* Observables of the current state (Sec. 3.5, last paragraph). */
 typedef struct {
