@@ -24,6 +24,9 @@ _LIB = os.path.join(_HERE, "libmpcd_oracle.so")
 
 FP64 = 0
 MIXED = 1
+# FP64 model of one mixed-model step: the float state streams in float (as in
+# MIXED); binning, sums, draws, xi and the collision are FP64
+FP64_FSTREAM = 2
 
 PURPOSE_SHIFT = 0x53484654
 PURPOSE_ROT = 0x524F5441
@@ -85,6 +88,8 @@ def _load():
         _lib.oracle_cos_sin_turn_f.argtypes = [ctypes.c_uint32, P(ctypes.c_float), P(ctypes.c_float)]
         _lib.oracle_log_f.argtypes = [ctypes.c_float]
         _lib.oracle_log_f.restype = ctypes.c_float
+        _lib.oracle_neg_log1m_f.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+        _lib.oracle_neg_log1m_f.restype = ctypes.c_float
         _lib.oracle_axis.argtypes = [u64, u64, ctypes.c_uint32, i32, P(d)]
         _lib.oracle_gamma_draw.argtypes = [u64, u64, ctypes.c_uint32, i32, d, i32, P(d)]
         _lib.oracle_gamma_draw.restype = i32
@@ -176,6 +181,12 @@ def cos_sin_turn_f(w: int):
 def log_f(x: float) -> float:
     """The mixed model's float natural logarithm."""
     return _load().oracle_log_f(float(np.float32(x)))
+
+
+def neg_log1m_f(hi: int, lo: int) -> float:
+    """The mixed model's float -ln(1 - U) for the 53-bit uniform U with words
+    (hi, lo): the squared Box-Muller radius over two."""
+    return _load().oracle_neg_log1m_f(int(hi) & 0xFFFFFFFF, int(lo) & 0xFFFFFFFF)
 
 
 def shift(seed: int, t: int) -> np.ndarray:

@@ -130,8 +130,41 @@ static float log_series_f(float x) {
   return (float)e * ln2 + (2.0f * t) * series;
 }
 
+/* -ln(1 - U) in float, the squared Box-Muller radius over two, for the 53-bit
+ * uniform U whose high and low words are hi and lo.  Three ranges, each free
+ * of cancellation:
+ *   U < 1/2              : 2 atanh(U / (2 - U)) = -ln(1 - U), U = hi 2^-32,
+ *                          the atanh series through t^15 (t <= 1/3);
+ *   1 - U >= 2^-12       : -ln(e), e = 1 - U = (2^32 - hi) 2^-32;
+ *   1 - U < 2^-12        : -ln(e) with e from all 53 bits,
+ *                          e = (2^53 - (hi 2^21 + lo / 2^11)) 2^-53,
+ *                          so that the radius's far tail is that of the FP64
+ *                          model's uniform (32 bits resolve e only to 2^-32). */
+static float neg_log1m_f(uint32_t hi, uint32_t lo) {
+  if (hi < 0x80000000u) {
+    const float U = (float)hi * 0x1p-32f;
+    const float t = U / (2.0f - U);
+    const float t2 = t * t;
+    const float l3 = (float)(1.0 / 3.0), l5 = (float)(1.0 / 5.0), l7 = (float)(1.0 / 7.0);
+    const float l9 = (float)(1.0 / 9.0), l11 = (float)(1.0 / 11.0), l13 = (float)(1.0 / 13.0);
+    const float l15 = (float)(1.0 / 15.0);
+    const float series =
+        1.0f + t2 * (l3 + t2 * (l5 + t2 * (l7 + t2 * (l9 + t2 * (l11 + t2 * (l13 + t2 * l15))))));
+    return (2.0f * t) * series;
+  }
+  float e;
+  if (hi < 0xFFF00000u) {
+    e = (float)(4294967296LL - (int64_t)hi) * 0x1p-32f;
+  } else {
+    const int64_t q = ((4294967296LL - (int64_t)hi) << 21) - (int64_t)(lo >> 11);
+    e = (float)q * 0x1p-53f;
+  }
+  return -log_series_f(e);
+}
+
 void oracle_cos_sin_turn_f(uint32_t w, float* c, float* s) { cos_sin_turn_f(w, c, s); }
 float oracle_log_f(float x) { return log_series_f(x); }
+float oracle_neg_log1m_f(uint32_t hi, uint32_t lo) { return neg_log1m_f(hi, lo); }
 
 /* ------------------------------------------------------------------------ */
 /* Sec. 2 / Sec. 3.4: random grid shift, one vector per step.  Quantised to  */
@@ -191,18 +224,18 @@ int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, 
     float kk = 1.5f * (float)(nc - 1);
     float d = kk - 1.0f / 3.0f;
     float c = 1.0f / sqrtf(9.0f * d);
-    float kTf = (float)kT;
     for (uint32_t j = 0; j < 64; ++j) {
       /* Attempt j: block A = counter (cell, 1 + 2j).  Its words 0, 2 and 1 are
-       * the high words of U1, U2 and U3 (the FP64 model takes the low words
-       * from block B), so the mixed model needs only block A. */
-      uint32_t wa[4];
+       * the high words of U1, U2 and U3; block B = (cell, 2 + 2j) holds their
+       * low words.  The mixed model reads a low word only for the radius's
+       * far tail (neg_log1m_f), else block A alone. */
+      uint32_t wa[4], wb[4];
       draw4(seed, ORACLE_PURPOSE_THERMO, cell, 1u + 2u * j, t, wa);
-      float e1 = (float)(4294967296LL - (int64_t)wa[0]) * 0x1p-32f;
+      draw4(seed, ORACLE_PURPOSE_THERMO, cell, 2u + 2u * j, t, wb);
       float U3 = (float)wa[1] * 0x1p-32f;
       float c2, s2;
       cos_sin_turn_f(wa[2], &c2, &s2);
-      float x = sqrtf(-2.0f * log_series_f(e1)) * c2;
+      float x = sqrtf(2.0f * neg_log1m_f(wa[0], wb[0])) * c2;
       float t1 = 1.0f + c * x;
       if (!(t1 > 0.0f)) continue;
       float v = t1 * t1 * t1;
@@ -210,14 +243,14 @@ int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, 
        * the acceptance region, so it accepts without the logarithms. */
       float x2 = x * x;
       if (U3 < 1.0f - 0.0331f * (x2 * x2)) {
-        *ehat = (double)(d * v * kTf);
+        *ehat = ((double)d * (double)v) * kT;
         return 0;
       }
       float lhs = log_series_f(U3);
       float rhs = 0.5f * x2 + d - d * v + d * log_series_f(v);
       int accept = lhs < rhs;
       if (accept) {
-        *ehat = (double)(d * v * kTf);
+        *ehat = ((double)d * (double)v) * kT;
         return 0;
       }
     }
@@ -257,12 +290,12 @@ void oracle_at_draw(uint64_t seed, uint64_t t, uint32_t tag, int32_t kind, doubl
                     int32_t precision, double dv[3]) {
   uint32_t wa[4];
   draw4(seed, ORACLE_PURPOSE_AT, tag, 2u * (uint32_t)kind, t, wa);
+  uint32_t wb[4];
+  draw4(seed, ORACLE_PURPOSE_AT, tag, 2u * (uint32_t)kind + 1u, t, wb);
   if (precision == ORACLE_MIXED) {
-    /* 1 - U = (2^32 - w) 2^-32 lies in (0, 1], so the logarithm is finite. */
-    float e1 = (float)(4294967296LL - (int64_t)wa[0]) * 0x1p-32f;
-    float e2 = (float)(4294967296LL - (int64_t)wa[2]) * 0x1p-32f;
-    float r1 = sqrtf(-2.0f * log_series_f(e1));
-    float r2 = sqrtf(-2.0f * log_series_f(e2));
+    /* radii from the high words (block B's low words only in the far tail) */
+    float r1 = sqrtf(2.0f * neg_log1m_f(wa[0], wb[0]));
+    float r2 = sqrtf(2.0f * neg_log1m_f(wa[2], wb[2]));
     float c1, s1, c2, s2;
     cos_sin_turn_f(wa[1], &c1, &s1);
     cos_sin_turn_f(wa[3], &c2, &s2);
@@ -272,8 +305,6 @@ void oracle_at_draw(uint64_t seed, uint64_t t, uint32_t tag, int32_t kind, doubl
     dv[2] = (double)(sg * (r2 * c2));
     return;
   }
-  uint32_t wb[4];
-  draw4(seed, ORACLE_PURPOSE_AT, tag, 2u * (uint32_t)kind + 1u, t, wb);
   double U1 = u01_53(wa[0], wb[0]), U2 = u01_53(wa[1], wb[1]);
   double U3 = u01_53(wa[2], wb[2]), U4 = u01_53(wa[3], wb[3]);
   double r1 = sqrt(-2.0 * log(1.0 - U1)), r2 = sqrt(-2.0 * log(1.0 - U3));
@@ -824,6 +855,11 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
                         double* spos, double* svel, uint64_t t, int32_t* cellid, cellbuf* cb,
                         int64_t ncells) {
   const int mixed = (p->precision == ORACLE_MIXED);
+  /* Float streaming: the mixed model, and the FP64 model of one mixed step
+   * (ORACLE_FP64_FSTREAM), which streams the float state as the mixed model
+   * does and takes every later stage in double. */
+  const int fstream = mixed || (p->precision == ORACLE_FP64_FSTREAM);
+  const int32_t arith = mixed ? ORACLE_MIXED : ORACLE_FP64;
   const double m = p->mass, Mb = p->solute_mass;
   const double ca = cos(p->alpha), sa = sin(p->alpha), omc = 1.0 - ca;
   int32_t status = 0;
@@ -837,7 +873,7 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
 
   /* Stream the solvent. */
   for (int64_t i = 0; i < n; ++i) {
-    if (mixed) {
+    if (fstream) {
       float r[3] = {(float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2]};
       float v[3] = {(float)vel[3 * i], (float)vel[3 * i + 1], (float)vel[3 * i + 2]};
       stream_f(p, r, v);
@@ -946,7 +982,7 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     }
     for (int64_t i = 0; i < n; ++i) {
       int32_t c = cellid[i];
-      oracle_at_draw(p->seed, t, (uint32_t)i, 0, sig, p->precision, dv);
+      oracle_at_draw(p->seed, t, (uint32_t)i, 0, sig, arith, dv);
       for (int k = 0; k < 3; ++k) {
         if (mixed) cb->Qd[3 * c + k] += llrint(dv[k] * 0x1p32);
         else cb->D[3 * c + k] += m * dv[k];
@@ -954,7 +990,7 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     }
     for (int64_t b = 0; b < nb; ++b) {
       int32_t c = cellid[n + b];
-      oracle_at_draw(p->seed, t, (uint32_t)b, 1, sigb, p->precision, dv);
+      oracle_at_draw(p->seed, t, (uint32_t)b, 1, sigb, arith, dv);
       for (int k = 0; k < 3; ++k) {
         if (mixed) cb->Qdx[3 * c + k] += llrint((Mb * dv[k]) * 0x1p32);
         else cb->D[3 * c + k] += Mb * dv[k];
@@ -974,7 +1010,7 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     }
     for (int64_t i = 0; i < n; ++i) {
       int32_t c = cellid[i];
-      oracle_at_draw(p->seed, t, (uint32_t)i, 0, sig, p->precision, dv);
+      oracle_at_draw(p->seed, t, (uint32_t)i, 0, sig, arith, dv);
       for (int k = 0; k < 3; ++k) {
         if (mixed) {
           float w = (float)cb->u[3 * c + k] + (float)dv[k];
@@ -986,7 +1022,7 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     }
     for (int64_t b = 0; b < nb; ++b) {
       int32_t c = cellid[n + b];
-      oracle_at_draw(p->seed, t, (uint32_t)b, 1, sigb, p->precision, dv);
+      oracle_at_draw(p->seed, t, (uint32_t)b, 1, sigb, arith, dv);
       for (int k = 0; k < 3; ++k)
         svel[3 * b + k] = (cb->u[3 * c + k] + dv[k]) - cb->dbar[3 * c + k];
     }
@@ -1039,21 +1075,20 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
   for (int64_t c = 0; c < ncells; ++c) {
     cb->xi[c] = 1.0;
     if (cb->cnt[c] == 0) continue;
-    oracle_axis(p->seed, t, (uint32_t)c, p->precision, &cb->axis[3 * c]);
+    oracle_axis(p->seed, t, (uint32_t)c, arith, &cb->axis[3 * c]);
     int32_t nc = cb->cnt[c] + cb->nvirt[c];
     if (p->thermostat && nc >= 2) {
+      /* Mixed model: E_k in double from the exact fixed-point sums, and
+       * xi = sqrt(E^/E_k) in double, rounded to the float that scales the
+       * float relative velocities. */
       double Ek;
-      if (mixed) {
-        float Ef = mf * (float)cb->Es[c] + (float)cb->Ex[c];
-        Ek = (double)((0.5f * Ef) * 0x1p-32f);
-      } else {
-        Ek = cb->E[c];
-      }
+      if (mixed) Ek = (0.5 * (m * (double)cb->Es[c] + (double)cb->Ex[c])) * 0x1p-32;
+      else Ek = cb->E[c];
       if (Ek > 0.0) {
         double ehat;
-        int32_t st = oracle_gamma_draw(p->seed, t, (uint32_t)c, nc, p->kT, p->precision, &ehat);
+        int32_t st = oracle_gamma_draw(p->seed, t, (uint32_t)c, nc, p->kT, arith, &ehat);
         if (st != 0) { status = st; continue; }
-        if (mixed) cb->xi[c] = (double)sqrtf((float)ehat / (float)Ek);
+        if (mixed) cb->xi[c] = (double)(float)sqrt(ehat / Ek);
         else cb->xi[c] = sqrt(ehat / Ek);
       }
     }
@@ -1107,6 +1142,9 @@ static int32_t check_params(const oracle_params* p, int64_t n, int64_t nb) {
   for (int k = 0; k < 3; ++k)
     if (p->n[k] < 1) return -1;
   if (n < 0 || nb < 0) return -1;
+  if (p->precision != ORACLE_FP64 && p->precision != ORACLE_MIXED &&
+      p->precision != ORACLE_FP64_FSTREAM)
+    return -1;
   if (!(p->dt > 0.0) || !(p->mass > 0.0) || !(p->kT >= 0.0)) return -1;
   if (p->walls_z && (p->g[2] != 0.0 || nb > 0)) return -1;
   if (p->collision != ORACLE_SRD && p->collision != ORACLE_AT) return -1;

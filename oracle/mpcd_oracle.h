@@ -28,12 +28,21 @@
  * lists them as future extensions); the reading implemented here is the one
  * the design notes state.
  *
- * Two arithmetic modes:
+ * Arithmetic modes:
  *   ORACLE_FP64  : every quantity in double; sums in particle-index order.
  *   ORACLE_MIXED : positions/velocities rounded to float after every store,
  *                  cell momentum/energy sums in int64 fixed point (scale 2^32),
- *                  rotation and thermostat draw in float with the operation
- *                  order fixed below; solute beads stay double.
+ *                  rotation and the thermostat's Gamma draw in float with the
+ *                  operation order fixed below; the thermostat factor
+ *                  xi = sqrt(E^/E_k) in double (then rounded to float);
+ *                  solute beads stay double.
+ *   ORACLE_FP64_FSTREAM : the FP64 model of one mixed-model step.  The float
+ *                  state streams as in ORACLE_MIXED (float fmaf, float wrap,
+ *                  positions and velocities stored as floats); binning, cell
+ *                  sums, the draws, xi and the collision are those of
+ *                  ORACLE_FP64.  From the same float state both modes see the
+ *                  same cells, so the velocities after one step measure the
+ *                  error of the mixed arithmetic alone.
  * State arrays are always passed as double; in MIXED mode they hold floats.
  */
 #ifndef MPCD_ORACLE_H
@@ -44,7 +53,7 @@
 extern "C" {
 #endif
 
-enum { ORACLE_FP64 = 0, ORACLE_MIXED = 1 };
+enum { ORACLE_FP64 = 0, ORACLE_MIXED = 1, ORACLE_FP64_FSTREAM = 2 };
 
 /* Random-stream purposes, XORed into the high key word (see oracle_key). */
 #define ORACLE_PURPOSE_SHIFT  0x53484654u
@@ -67,7 +76,7 @@ typedef struct {
   int32_t walls_z;       /* 1 = bounce-back walls at z = 0 and z = n_z      */
   double g[3];           /* body-force acceleration (g[2] must be 0 w/ walls)*/
   double virt_density;   /* virtual-particle density in wall-cut cells      */
-  int32_t precision;     /* ORACLE_FP64 or ORACLE_MIXED                     */
+  int32_t precision;     /* ORACLE_FP64, ORACLE_MIXED or ORACLE_FP64_FSTREAM */
   int32_t chain_len;     /* beads per chain (solute)                        */
   int32_t md_substeps;   /* velocity-Verlet substeps per collision          */
   int32_t collision;     /* ORACLE_SRD (Eq. srd) or ORACLE_AT (Eq. at)      */
@@ -87,6 +96,10 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
  * cos and sin of 2 pi w / 2^32, and the natural logarithm. */
 void oracle_cos_sin_turn_f(uint32_t w, float* c, float* s);
 float oracle_log_f(float x);
+/* The mixed model's float -ln(1 - U) for the 53-bit uniform U with high and
+ * low words hi, lo (the squared Box-Muller radius over two); lo is used only
+ * when 1 - U < 2^-12. */
+float oracle_neg_log1m_f(uint32_t hi, uint32_t lo);
 
 /* Grid shift of step t: s_k = S_k * 2^-32, S_k in [-2^31, 2^31). */
 void oracle_shift(uint64_t seed, uint64_t t, double s[3]);
@@ -98,7 +111,10 @@ void oracle_axis(uint64_t seed, uint64_t t, uint32_t cell, int32_t precision, do
  * Gamma(3(nc-1)/2, kT) by Marsaglia-Tsang with its squeeze.  Attempt j reads
  * Philox block A = counter (cell, 1 + 2j): words 0, 2, 1 are the high words
  * of the uniforms U1, U2, U3 (Box-Muller from U1, U2; acceptance from U3);
- * the FP64 model takes their low words from block B = (cell, 2 + 2j).
+ * the FP64 model takes their low words from block B = (cell, 2 + 2j), the
+ * mixed model only the low word of U1 when 1 - U1 < 2^-12.  In the mixed
+ * model the normal, the squeeze and the acceptance are float and
+ * E^ = (d v) kT is formed in double from the float d and v.
  * Returns 0, or -4 if 64 attempts were all rejected. */
 int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc,
                           double kT, int32_t precision, double* ehat);

@@ -124,19 +124,6 @@ def test_thermostat_energy_is_gamma_distributed(nc, precision):
     assert abs(e.var() / (shape * kT**2) - 1.0) < 0.12
 
 
-def test_thermostat_mixed_draw_tracks_fp64_draw():
-    """Both precisions consume the same counters; with float uniforms that are the
-    top 24 bits of the double ones, accepted draws agree closely when the same
-    attempt is accepted."""
-    close = 0
-    for c in range(300):
-        a = oracle.gamma_draw(4, 7, c, 6, 1.0, oracle.FP64)
-        b = oracle.gamma_draw(4, 7, c, 6, 1.0, oracle.MIXED)
-        if abs(a - b) <= 1e-5 * max(1.0, a):
-            close += 1
-    assert close >= 295
-
-
 def _ulp32(x):
     x = np.abs(np.asarray(x, dtype=np.float32))
     return np.spacing(np.maximum(x, np.float32(2.0**-126))).astype(np.float64)

@@ -248,24 +248,6 @@ def test_resume_is_bit_exact():
     assert np.array_equal(a.vel, b.vel) and np.array_equal(a.pos, b.pos)
 
 
-def test_mixed_tracks_fp64_within_1e6_per_step():
-    """One step from the same float-representable state: the mixed model (FP32
-    particles, fixed-point sums, FP32 rotation) stays within 1e-6 relative of
-    the FP64 oracle, |dv| / max(|v|, sqrt(kT/m)), with identical cells."""
-    for thermostat in (False, True):
-        pd = oracle.Params(n=(10, 10, 10), seed=6, thermostat=thermostat)
-        pm = oracle.Params(n=(10, 10, 10), seed=6, thermostat=thermostat,
-                           precision=oracle.MIXED)
-        a = _state(pd.n, 5, seed=6, mixed=True)
-        b = a.copy()
-        ca, _ = oracle.step(pd, a, 1, want_cells=True)
-        cb, _ = oracle.step(pm, b, 1, want_cells=True)
-        assert np.array_equal(ca, cb)
-        err = np.linalg.norm(a.vel - b.vel, axis=1) / np.maximum(np.linalg.norm(a.vel, axis=1), 1)
-        assert err.max() < 1e-6
-        assert np.max(np.abs(a.pos - b.pos)) < 1e-5
-
-
 def test_observables_initial_state():
     p = oracle.Params(n=(10, 10, 10))
     st = _state(p.n, 10, seed=4)
