@@ -187,12 +187,13 @@ void oracle_axis(uint64_t seed, uint64_t t, uint32_t cell, int32_t precision, do
   uint32_t w[4];
   draw4(seed, ORACLE_PURPOSE_ROT, cell, 0u, t, w);
   /* z = 2u - 1 and sqrt(1 - z^2) = 2 sqrt(u (1 - u)) with u = w0 / 2^32, so
-   * that 1 - u is exact and the pole region keeps full relative precision. */
+   * that 1 - u is exact and the pole region keeps full relative precision.
+   * The mixed model takes u (1 - u) 2^64 = w0 (2^32 - w0) as an exact 64-bit
+   * integer product, rounded once to float. */
   if (precision == ORACLE_MIXED) {
-    float a = (float)w[0] * 0x1p-32f;
-    float b = (float)(4294967296LL - (int64_t)w[0]) * 0x1p-32f;
     float z = (float)(2LL * (int64_t)w[0] - 4294967296LL) * 0x1p-32f;
-    float r = 2.0f * sqrtf(a * b);
+    uint64_t q = (uint64_t)w[0] * (uint64_t)(4294967296ULL - (uint64_t)w[0]);
+    float r = 2.0f * sqrtf((float)q * 0x1p-64f);
     float cphi, sphi;
     cos_sin_turn_f(w[1], &cphi, &sphi);
     n[0] = (double)(r * cphi);
