@@ -1394,11 +1394,12 @@ void mpcd_batch_destroy(mpcd_batch* bt) { delete bt; }
 // Allocation-free variant of mpcd_profile.
 //
 // Some callers cannot allocate device memory at the moment they want a
-// profile: code running while a CUDA stream is being captured into a graph
-// (cudaMalloc / cudaMallocAsync are not allowed there), and services that run
-// inside a fixed, pre-reserved device-memory budget where every allocation
-// is accounted for up front.  This entry point uses only memory that already
-// exists: the box's own arrays and a static per-bin scratch array below.
+// profile: services that run inside a fixed, pre-reserved device-memory
+// budget where every allocation is accounted for up front, and job servers
+// that keep nearly all of the GPU's memory filled with resident boxes, where
+// an allocation at query time could fail.  This entry point uses only memory
+// that already exists: the box's own arrays and a static per-bin scratch
+// array below.  It synchronises the box's stream to read the result back.
 // ===========================================================================
 namespace {
 

@@ -154,8 +154,8 @@ __device__ __forceinline__ float series_log(float x) {
   return (e >= 0 ? small_to_float(e) : -small_to_float(-e)) * ln2 + (2.0f * t) * series;
 }
 
-// series_log for 2^-32 <= x <= 1 (a normal positive float): the same
-// operations without the special cases.
+// series_log for a normal positive float x <= 1: the same operations without
+// the special cases.
 __device__ __forceinline__ float series_log_unit(float x) {
   uint32_t b = __float_as_uint(x);
   int e = (int)((b >> 23) & 0xFFu) - 127;
@@ -173,13 +173,48 @@ __device__ __forceinline__ float series_log_unit(float x) {
   return (e >= 0 ? small_to_float(e) : -small_to_float(-e)) * ln2 + (2.0f * t) * series;
 }
 
+// rne(q) as a float for 0 <= q < 2^63, on the integer pipe.
+__device__ __forceinline__ float u63_to_float(unsigned long long q) { return i64_to_float((long long)q); }
+
+// -ln(1 - U) in float (the squared Box-Muller radius over two) for the 53-bit
+// uniform U with high word hi; lo_of() supplies its low word and is called
+// only when 1 - U < 2^-12.  U < 1/2: 2 atanh(U / (2 - U)) with U = hi 2^-32
+// (series through t^15, t <= 1/3), free of the cancellation of 1 - U near 1;
+// otherwise -ln(e), e = 1 - U = (2^32 - hi) 2^-32, or, in the far tail, e
+// from all 53 bits, (2^32 - hi) 2^21 - lo / 2^11 in units of 2^-53, so that
+// the radius follows the FP64 model's uniform there.
+template <class LoOf>
+__device__ __forceinline__ float neg_log1m(uint32_t hi, LoOf lo_of) {
+  if (hi < 0x80000000u) {
+    const float U = word_to_float(hi) * 0x1p-32f;
+    const float t = U / (2.0f - U);
+    const float t2 = t * t;
+    const float l3 = (float)(1.0 / 3.0), l5 = (float)(1.0 / 5.0), l7 = (float)(1.0 / 7.0);
+    const float l9 = (float)(1.0 / 9.0), l11 = (float)(1.0 / 11.0), l13 = (float)(1.0 / 13.0);
+    const float l15 = (float)(1.0 / 15.0);
+    const float series =
+        1.0f + t2 * (l3 + t2 * (l5 + t2 * (l7 + t2 * (l9 + t2 * (l11 + t2 * (l13 + t2 * l15))))));
+    return (2.0f * t) * series;
+  }
+  float e;
+  if (hi < 0xFFF00000u) {
+    e = comp_word_to_float(hi) * 0x1p-32f;
+  } else {
+    const uint32_t lo = lo_of();
+    const unsigned long long q =
+        ((unsigned long long)(0u - hi) << 21) - (unsigned long long)(lo >> 11);
+    e = u63_to_float(q) * 0x1p-53f;
+  }
+  return -series_log_unit(e);
+}
+
 __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, uint32_t cell,
                                         float n[3]) {
   const uint4 w = draw(B, PURPOSE_ROT, cell, 0u, t);
-  const float a = word_to_float(w.x) * 0x1p-32f;
-  const float b = comp_word_to_float(w.x) * 0x1p-32f;
   const float z = centred_word_half_to_float(w.x) * 0x1p-31f;
-  const float r = 2.0f * sqrtf(a * b);
+  // sqrt(1 - z^2) = 2 sqrt(u (1 - u)), u (1 - u) 2^64 = w (2^32 - w) exact in 64 bits
+  const unsigned long long q = (unsigned long long)w.x * (unsigned long long)(0u - w.x);
+  const float r = 2.0f * sqrtf(u63_to_float(q) * 0x1p-64f);
   float c, s;
   turn_cos_sin(w.y, c, s);
   n[0] = r * c;
@@ -205,22 +240,24 @@ __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, u
 // Box-Muller normal and the squeeze U3 < 1 - 0.0331 x^4 (inside the acceptance
 // region, so it accepts without logarithms).  Attempt j reads Philox block
 // A = counter (cell, 1 + 2j): words 0, 2, 1 are the high words of U1, U2, U3;
-// the FP64 sampler takes the low words from block B = (cell, 2 + 2j).  The
-// float version decides every acceptance in float, with the same series as
-// the oracle's mixed model.  Returns false after 64 rejections.
+// their low words are in block B = (cell, 2 + 2j).  gamma_draw_mixed, the
+// mixed model's sampler, decides every acceptance in float with the series
+// above (block B only for the far tail of the radius, see neg_log1m) and
+// forms E^ = (d v) kT in double from the float d and v; gamma_draw is the
+// FP64 sampler.  Both return false after 64 rejections.
 // ---------------------------------------------------------------------------
-__device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
-                                  float& ehat) {
+__device__ inline bool gamma_draw_mixed(const BoxDev& B, unsigned long long t, uint32_t cell,
+                                        int nc, double& ehat) {
   const float kk = 1.5f * small_to_float(nc - 1);
   const float d = kk - 1.0f / 3.0f;
   const float c = 1.0f / sqrtf(9.0f * d);
   for (uint32_t j = 0; j < 64u; ++j) {
     const uint4 wa = draw(B, PURPOSE_THERMO, cell, 1u + 2u * j, t);
-    const float e1 = comp_word_to_float(wa.x) * 0x1p-32f;
     const float U3 = word_to_float(wa.y) * 0x1p-32f;
     float c2, s2;
     turn_cos_sin(wa.z, c2, s2);
-    const float x = sqrtf(-2.0f * series_log(e1)) * c2;
+    const float L = neg_log1m(wa.x, [&] { return draw(B, PURPOSE_THERMO, cell, 2u + 2u * j, t).x; });
+    const float x = sqrtf(2.0f * L) * c2;
     const float t1 = 1.0f + c * x;
     if (!(t1 > 0.0f)) continue;
     const float v = t1 * t1 * t1;
@@ -228,7 +265,7 @@ __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_
     bool accept = U3 < 1.0f - 0.0331f * (x2 * x2);
     if (!accept) accept = series_log(U3) < 0.5f * x2 + d - d * v + d * series_log(v);
     if (accept) {
-      ehat = d * v * B.kT_f;
+      ehat = __dmul_rn(__dmul_rn((double)d, (double)v), B.kT);
       return true;
     }
   }
@@ -263,16 +300,17 @@ __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_
 // solvent, 1 the solute beads.  Box-Muller on Philox block A = counter
 // (tag, 2 kind): words (0, 1) give components 0 and 1 (cos and sin
 // branches), words (2, 3) component 2 (cos).  The float version stays in
-// float with the mixed model's series; the FP64 version takes the low words
-// of its 53-bit uniforms from block B = (tag, 2 kind + 1).
+// float with the mixed model's series (block B = (tag, 2 kind + 1) only for
+// the far tail of a radius, see neg_log1m); the FP64 version takes the low
+// words of its 53-bit uniforms from block B.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void at_draw(const BoxDev& B, unsigned long long t, uint32_t tag,
                                         uint32_t kind, float sigma, float dv[3]) {
   const uint4 w = draw(B, PURPOSE_AT, tag, 2u * kind, t);
-  const float e1 = comp_word_to_float(w.x) * 0x1p-32f;  // 1 - U in (0, 1]
-  const float e2 = comp_word_to_float(w.z) * 0x1p-32f;
-  const float r1 = sqrtf(-2.0f * series_log_unit(e1));
-  const float r2 = sqrtf(-2.0f * series_log_unit(e2));
+  const float r1 =
+      sqrtf(2.0f * neg_log1m(w.x, [&] { return draw(B, PURPOSE_AT, tag, 2u * kind + 1u, t).x; }));
+  const float r2 =
+      sqrtf(2.0f * neg_log1m(w.z, [&] { return draw(B, PURPOSE_AT, tag, 2u * kind + 1u, t).z; }));
   float c1, s1, c2, s2;
   turn_cos_sin(w.y, c1, s1);
   turn_cos_sin(w.w, c2, s2);
@@ -388,10 +426,10 @@ template <> struct CellAcc<true> {
     const double e = d0 * d0 + d1 * d1 + d2 * d2;
     ex += __double2ll_rn((mass * e) * 4294967296.0);
   }
-  __device__ __forceinline__ float energy(const BoxDev& B, bool extra) const {
-    float E = B.m_f * i64_to_float(es);
-    if (extra) E = E + i64_to_float(ex);
-    return (0.5f * E) * 0x1p-32f;
+  // E_k in double from the exact sums (the thermostat factor is FP64).
+  __device__ __forceinline__ double energy(const BoxDev& B, bool) const {
+    return __dmul_rn(__dmul_rn(0.5, __dadd_rn(__dmul_rn(B.m, __ll2double_rn(es)), __ll2double_rn(ex))),
+                     0x1p-32);
   }
   __device__ __forceinline__ void add_energy_partial(const CellAcc& o) { es += o.es; }
 };
@@ -522,16 +560,17 @@ __device__ __forceinline__ void cell_finish(const BoxDev& B, unsigned long long 
         a.add_extra_energy(B.m, vv, u);
       }
     }
+    // Eq. thermo: xi = sqrt(E^ / E_k), in FP64 in both models (the mixed
+    // model rounds it to the float that scales its relative velocities)
     const int nc = a.ns + a.nb + a.nv;
-    const T Ek = a.energy(B, extra);
-    if (nc >= 2 && Ek > (T)0) {
-      T ehat;
-      if (gamma_draw(B, t, cell, nc, ehat)) {
-        if constexpr (MIXED) xi = sqrtf(ehat / Ek);
-        else xi = sqrt(ehat / Ek);
-      } else {
-        atomicOr(err, ERR_GAMMA_CAP);
-      }
+    const double Ek = a.energy(B, extra);
+    if (nc >= 2 && Ek > 0.0) {
+      double ehat;
+      bool ok;
+      if constexpr (MIXED) ok = gamma_draw_mixed(B, t, cell, nc, ehat);
+      else ok = gamma_draw(B, t, cell, nc, ehat);
+      if (ok) xi = (T)sqrt(ehat / Ek);
+      else atomicOr(err, ERR_GAMMA_CAP);
     }
   }
 #pragma unroll

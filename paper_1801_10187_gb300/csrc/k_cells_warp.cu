@@ -661,15 +661,17 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
             for (uint32_t j = 0; j < novf; ++j)
               if (ovf_cell[j] == (uint32_t)cell) add_energy(ovf + j);
           if (BEADS && gnb > 0) Ex = (long long)BS.E[lane];
-          // Eq. thermo: E_k about u, E^ ~ Gamma(3(N_c-1)/2, kT), xi = sqrt(E^/E_k)
-          float E = H.m * (exact64_e ? i64_to_float(Es)
-                                     : split_sum_to_float(W.h[0][lane], W.l[0][lane], Es));
-          if (BEADS) E = E + i64_to_float(Ex);
-          const float Ek = (0.5f * E) * 0x1p-32f;
+          // Eq. thermo: E_k about u, E^ ~ Gamma(3(N_c-1)/2, kT), and
+          // xi = sqrt(E^/E_k) in FP64 from the exact sums, rounded to float
+          const long long Etot =
+              exact64_e ? Es : (long long)W.h[0][lane] * 1048576LL + (long long)W.l[0][lane] + Es;
+          const double Ek = __dmul_rn(
+              __dmul_rn(0.5, __dadd_rn(__dmul_rn(B.m, __ll2double_rn(Etot)), __ll2double_rn(Ex))),
+              0x1p-32);
           const int nc = (int)n + nb;
-          if (nc >= 2 && Ek > 0.0f) {
-            float ehat;
-            if (gamma_draw(B, t, (uint32_t)cell, nc, ehat)) xi = sqrtf(ehat / Ek);
+          if (nc >= 2 && Ek > 0.0) {
+            double ehat;
+            if (gamma_draw_mixed(B, t, (uint32_t)cell, nc, ehat)) xi = __double2float_rn(sqrt(ehat / Ek));
             else atomicOr(err, ERR_GAMMA_CAP);
           }
         }

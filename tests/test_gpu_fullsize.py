@@ -14,7 +14,16 @@ launch per step), against the oracle run on the same states.
   * the paper's polymer benchmark (1.25e6 FP64 solvent particles, 1024 chains
     of 50 repelling beads): total momentum and energy conserved.
 Tolerances as in the small parity tests: mixed bit-exact, FP64 1e-12
-relative per step.  These runs take a few minutes of oracle time.
+relative per step.
+
+The mixed model's accuracy at full size: one GPU step of the 10^7-particle
+box (SRD with and without the thermostat, the Andersen rule, the angular
+correction) and of the 7.8 * 10^7-particle solute + thermostat box against
+the FP64 model run from the same float state with float streaming (the same
+cells), every particle within the bound of tests/mixed_bound.py; cells whose
+float and FP64 Gamma samplers accept different attempts are counted and left
+out.  The maximum error, the particles above 1e-6 and the flips are shown in
+the run's summary.  These runs take a few minutes of oracle time.
 """
 import math
 
@@ -23,6 +32,8 @@ import pytest
 
 import oracle
 from paper_1801_10187_gb300 import inputs
+
+from mixed_bound import gamma_flip_cells, inertia_condition, mixed_step_bound, rel_errors
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -103,6 +114,67 @@ def test_fullsize_78m_solute_thermostat():
     spos, svel, ref = run_full("srd-250c-rho5-mixed-solute")
     assert rel_err(svel, ref.svel, m=5.0) == 0.0
     assert np.max(np.abs(spos - ref.spos)) <= 1e-11
+
+
+MIXED_CASES = [("srd-100c-rho10-mixed", False), ("srd-100c-rho10-mixed", True),
+               ("srd-100c-rho10-mixed-at", False), ("srd-100c-rho10-mixed-angular", False),
+               ("srd-250c-rho5-mixed-solute", True)]
+
+
+@pytest.mark.parametrize("name,thermostat", MIXED_CASES)
+def test_fullsize_mixed_against_fp64_one_step(name, thermostat, report):
+    cfg = W[name]
+    kw = box_kw(cfg)
+    kw["thermostat"] = thermostat
+    t0 = 31
+    s = inputs.solvent(cfg["n"], cfg["density"], kT=cfg["kT"], seed=cfg["seed"], mixed=True)
+    sp = sv = np.zeros((0, 3))
+    if cfg.get("n_chains"):
+        sp, sv = inputs.chains(cfg["n"], cfg["n_chains"], cfg["chain_len"], cfg["bond_r0"],
+                               kT=cfg["kT"], bead_mass=cfg["bead_mass"], seed=cfg["seed"] + 1000)
+    box = pkg.Box(**kw)
+    box.set_state(s.pos, s.vel, sp if len(sp) else None, sv if len(sv) else None, step=t0)
+    box.step(1)
+    pos, vel, spos, svel, st = box.get_state()
+    cells, counts = box.last_cells()
+    box.close()
+    p = oracle_params(kw)
+    p.precision = oracle.FP64_FSTREAM
+    ref = oracle.State(np.asarray(s.pos, np.float64), np.asarray(s.vel, np.float64),
+                       sp.copy(), sv.copy(), step=t0)
+    rc, rk = oracle.step(p, ref, 1, want_cells=True)
+    ns = s.pos.shape[0]
+    assert st == ref.step == t0 + 1
+    np.testing.assert_array_equal(cells, rc)
+    np.testing.assert_array_equal(counts, rk)
+    np.testing.assert_array_equal(pos, ref.pos)
+    if len(sp):
+        assert np.max(np.abs(spos - ref.spos)) <= 1e-11
+    cond = (inertia_condition(ref.pos, rc[:ns], oracle.shift(kw["seed"], t0), kw["n"], rk.shape[0])
+            if kw["angular"] else None)
+    M = kw.get("solute_mass", 1.0)
+    bound, bbound = mixed_step_bound(s.vel, ref.vel, rc[:ns], kT=kw["kT"], thermostat=thermostat,
+                                     svel_ref=ref.svel, bead_cells=rc[ns:], bead_mass=M,
+                                     angular_cond=cond)
+    err = rel_errors(vel, ref.vel, kT=kw["kT"])
+    over = err > bound
+    flips = np.zeros(0, dtype=np.int64)
+    if thermostat:
+        flips = gamma_flip_cells(kw["seed"], t0, kw["kT"], rk, rc[:ns][over])
+        over &= ~np.isin(rc[:ns], flips)
+    occupied = int(np.count_nonzero(rk))
+    line = (f"mixed vs FP64, one step, {name}{' +thermostat' if thermostat else ''}: "
+            f"{ns} particles, max rel err {err.max():.3g}, above 1e-6: {int(np.sum(err > 1e-6))}, "
+            f"max err/bound {np.max(err / bound):.3g} outside flipped cells, Gamma flips "
+            f"{len(flips)} of {occupied} cells")
+    if len(sp):
+        eb = rel_errors(svel, ref.svel, kT=kw["kT"], m=M)
+        bover = (eb > bbound) & ~np.isin(rc[ns:], flips)
+        assert not bover.any()
+        line += f", beads max rel err {eb.max():.3g}"
+    report.append(line)
+    assert not over.any(), line
+    assert len(flips) <= 5 + 1e-6 * occupied, line
 
 
 def test_fullsize_batch64():
