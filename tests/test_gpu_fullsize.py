@@ -140,8 +140,8 @@ def test_fullsize_mixed_against_fp64_one_step(name, thermostat, report):
     box.close()
     p = oracle_params(kw)
     p.precision = oracle.FP64_FSTREAM
-    ref = oracle.State(np.asarray(s.pos, np.float64), np.asarray(s.vel, np.float64),
-                       sp.copy(), sv.copy(), step=t0)
+    # copies: the oracle steps its state in place, and s.vel is needed below
+    ref = oracle.State(s.pos.copy(), s.vel.copy(), sp.copy(), sv.copy(), step=t0)
     rc, rk = oracle.step(p, ref, 1, want_cells=True)
     ns = s.pos.shape[0]
     assert st == ref.step == t0 + 1
