@@ -90,6 +90,8 @@ def _load():
         _lib.oracle_log_f.restype = ctypes.c_float
         _lib.oracle_neg_log1m_f.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
         _lib.oracle_neg_log1m_f.restype = ctypes.c_float
+        _lib.oracle_xi_mixed.argtypes = [ctypes.c_double, ctypes.c_double]
+        _lib.oracle_xi_mixed.restype = ctypes.c_float
         _lib.oracle_axis.argtypes = [u64, u64, ctypes.c_uint32, i32, P(d)]
         _lib.oracle_gamma_draw.argtypes = [u64, u64, ctypes.c_uint32, i32, d, i32, P(d)]
         _lib.oracle_gamma_draw.restype = i32
@@ -181,6 +183,11 @@ def cos_sin_turn_f(w: int):
 def log_f(x: float) -> float:
     """The mixed model's float natural logarithm."""
     return _load().oracle_log_f(float(np.float32(x)))
+
+
+def xi_mixed(ehat: float, ek: float) -> float:
+    """The mixed model's thermostat factor sqrt(ehat / ek), float."""
+    return _load().oracle_xi_mixed(float(ehat), float(ek))
 
 
 def neg_log1m_f(hi: int, lo: int) -> float:

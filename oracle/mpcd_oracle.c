@@ -162,6 +162,8 @@ static float neg_log1m_f(uint32_t hi, uint32_t lo) {
   return -log_series_f(e);
 }
 
+static float xi_mixed(double H, double E);
+float oracle_xi_mixed(double ehat, double ek) { return xi_mixed(ehat, ek); }
 void oracle_cos_sin_turn_f(uint32_t w, float* c, float* s) { cos_sin_turn_f(w, c, s); }
 float oracle_log_f(float x) { return log_series_f(x); }
 float oracle_neg_log1m_f(uint32_t hi, uint32_t lo) { return neg_log1m_f(hi, lo); }
@@ -828,6 +830,23 @@ static void rotate_f(const float n[3], float ca, float sa, float omc, const floa
   for (int k = 0; k < 3; ++k) out[k] = fmaf(n[k], ndo, fmaf(cr[k], sa, d[k] * ca));
 }
 
+/* Mixed model, Eq. (thermo): xi = sqrt(E^/E_k) to double accuracy, rounded
+ * to float.  The float estimate y0 = sqrt(RN(E^)/RN(E_k)) (about 1e-7
+ * relative) is refined by one Newton step in double,
+ *   y1 = y0 + (E^ - y0^2 E_k) / (2 y0 E_k),
+ * the residual by one fused multiply-add (y0^2 is exact in double) and the
+ * step's 1/(2 y0 E_k) in float: its rounding scales a correction of relative
+ * size 1e-7, so y1 is within a few 1e-14 of the square root.  E^ = 0 (kT = 0)
+ * gives xi = 0. */
+static float xi_mixed(double H, double E) {
+  const float Ef = (float)E;
+  const float y0 = sqrtf((float)H / Ef);
+  if (!(y0 > 0.0f)) return y0;
+  const double r = fma(-((double)y0 * (double)y0), E, H);
+  const float inv = 0.5f / (y0 * Ef);
+  return (float)fma(r, (double)inv, (double)y0);
+}
+
 /* ------------------------------------------------------------------------ */
 /* One SRD step (Sec. 3 step flow)                                           */
 /* ------------------------------------------------------------------------ */
@@ -1079,17 +1098,18 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     oracle_axis(p->seed, t, (uint32_t)c, arith, &cb->axis[3 * c]);
     int32_t nc = cb->cnt[c] + cb->nvirt[c];
     if (p->thermostat && nc >= 2) {
-      /* Mixed model: E_k in double from the exact fixed-point sums, and
-       * xi = sqrt(E^/E_k) in double, rounded to the float that scales the
+      /* Mixed model: E_k in double from the exact fixed-point sums (mass and
+       * the factor 1/2 applied as exact scalings), and xi = sqrt(E^/E_k) to
+       * double accuracy (xi_mixed), rounded to the float that scales the
        * float relative velocities. */
       double Ek;
-      if (mixed) Ek = (0.5 * (m * (double)cb->Es[c] + (double)cb->Ex[c])) * 0x1p-32;
+      if (mixed) Ek = fma(0x1p-33, (double)cb->Ex[c], (0.5 * m * 0x1p-32) * (double)cb->Es[c]);
       else Ek = cb->E[c];
       if (Ek > 0.0) {
         double ehat;
         int32_t st = oracle_gamma_draw(p->seed, t, (uint32_t)c, nc, p->kT, arith, &ehat);
         if (st != 0) { status = st; continue; }
-        if (mixed) cb->xi[c] = (double)(float)sqrt(ehat / Ek);
+        if (mixed) cb->xi[c] = (double)xi_mixed(ehat, Ek);
         else cb->xi[c] = sqrt(ehat / Ek);
       }
     }

@@ -100,6 +100,9 @@ float oracle_log_f(float x);
  * low words hi, lo (the squared Box-Muller radius over two); lo is used only
  * when 1 - U < 2^-12. */
 float oracle_neg_log1m_f(uint32_t hi, uint32_t lo);
+/* The mixed model's thermostat factor sqrt(ehat / ek) (ehat, ek > 0): a float
+ * estimate refined by one FP64 Newton step, then rounded to float. */
+float oracle_xi_mixed(double ehat, double ek);
 
 /* Grid shift of step t: s_k = S_k * 2^-32, S_k in [-2^31, 2^31). */
 void oracle_shift(uint64_t seed, uint64_t t, double s[3]);

@@ -235,6 +235,29 @@ __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, u
   n[2] = z;
 }
 
+// Mixed model, Eq. (thermo): xi = sqrt(E^/E_k) to double accuracy, rounded to
+// float.  The float estimate y0 = sqrt(RN(E^)/RN(E_k)) is refined by one
+// Newton step in double, y1 = y0 + (E^ - y0^2 E_k) / (2 y0 E_k): the residual
+// by one fused multiply-add (y0^2 is exact in double), the step's
+// 1/(2 y0 E_k) in float (its rounding scales a correction of relative size
+// 1e-7).  About a dozen FP64-pipe instructions per cell instead of the two
+// dozen of a double division and square root.  E^ = 0 gives xi = 0.
+__device__ __forceinline__ float xi_mixed(double H, double E) {
+  const float Ef = __double2float_rn(E);
+  const float y0 = sqrtf(__fdiv_rn(__double2float_rn(H), Ef));
+  if (!(y0 > 0.0f)) return y0;
+  const double r = __fma_rn(-__dmul_rn((double)y0, (double)y0), E, H);
+  const float inv = __fdiv_rn(0.5f, __fmul_rn(y0, Ef));
+  return __double2float_rn(__fma_rn(r, (double)inv, (double)y0));
+}
+
+// E_k of the mixed model in double from the exact sums: solvent sum es of
+// rne(|v - u|^2 2^32) (mass factored out) and the beads' and virtual
+// particles' sum ex of rne(m |v - u|^2 2^32); m and 1/2 enter as exact scalings.
+__device__ __forceinline__ double mixed_energy(double m, long long es, long long ex) {
+  return __fma_rn(0x1p-33, __ll2double_rn(ex), __dmul_rn(0.5 * m * 0x1p-32, __ll2double_rn(es)));
+}
+
 // ---------------------------------------------------------------------------
 // Eq. (thermo) / Sec. 3.6: E^ ~ Gamma(3(Nc-1)/2, kT) by Marsaglia-Tsang with a
 // Box-Muller normal and the squeeze U3 < 1 - 0.0331 x^4 (inside the acceptance
@@ -428,8 +451,7 @@ template <> struct CellAcc<true> {
   }
   // E_k in double from the exact sums (the thermostat factor is FP64).
   __device__ __forceinline__ double energy(const BoxDev& B, bool) const {
-    return __dmul_rn(__dmul_rn(0.5, __dadd_rn(__dmul_rn(B.m, __ll2double_rn(es)), __ll2double_rn(ex))),
-                     0x1p-32);
+    return mixed_energy(B.m, es, ex);
   }
   __device__ __forceinline__ void add_energy_partial(const CellAcc& o) { es += o.es; }
 };
@@ -569,8 +591,9 @@ __device__ __forceinline__ void cell_finish(const BoxDev& B, unsigned long long 
       bool ok;
       if constexpr (MIXED) ok = gamma_draw_mixed(B, t, cell, nc, ehat);
       else ok = gamma_draw(B, t, cell, nc, ehat);
-      if (ok) xi = (T)sqrt(ehat / Ek);
-      else atomicOr(err, ERR_GAMMA_CAP);
+      if (!ok) atomicOr(err, ERR_GAMMA_CAP);
+      else if constexpr (MIXED) xi = xi_mixed(ehat, Ek);
+      else xi = sqrt(ehat / Ek);
     }
   }
 #pragma unroll

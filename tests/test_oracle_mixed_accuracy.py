@@ -49,6 +49,21 @@ def test_neg_log1m_float_matches_log1p():
     assert np.all(np.isfinite(got))
 
 
+def test_xi_mixed_is_the_rounded_square_root():
+    """The mixed thermostat factor (float estimate plus one FP64 Newton step)
+    equals the float nearest to sqrt(E^/E_k) computed in extended precision,
+    over E^ and E_k spanning ten decades each (Eq. thermo)."""
+    rng = np.random.default_rng(9)
+    H = 10.0 ** rng.uniform(-5, 5, 20000)
+    E = 10.0 ** rng.uniform(-5, 5, 20000)
+    got = np.array([oracle.xi_mixed(h, e) for h, e in zip(H, E)], dtype=np.float32)
+    want = np.sqrt(H.astype(np.longdouble) / E.astype(np.longdouble)).astype(np.float32)
+    assert np.mean(got == want) >= 0.9999
+    assert np.all(np.abs(got.astype(np.float64) - want.astype(np.float64))
+                  <= np.spacing(want).astype(np.float64))
+    assert oracle.xi_mixed(0.0, 1.0) == 0.0
+
+
 def test_fstream_equals_fp64_when_float_streaming_is_exact():
     """With dt = 1/8 and positions and velocities on a 2^-8 grid, every float
     stream operation is exact, so the FP64 model with float streaming is the
