@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """SRD (MPCD) step throughput on GB300: particle-steps/s and HBM roofline.
 
-Default workload: the 100 x 100 x 100-cell SRD solvent at 10 particles per
-cell (10^7 particles), mixed precision (FP32 particles, int64 fixed-point cell
-sums), alpha = 130 deg, dt = 0.1, kT = 1, grid shift every step, reorder every
-25 steps, 2000 steps.  Synthetic, seeded inputs (uniform positions,
-zero-momentum Maxwell-Boltzmann velocities).
+Default workload: the 250 x 250 x 250-cell SRD solvent at 5 particles per
+cell (7.8 * 10^7 particles) in mixed precision (FP32 particles, int64
+fixed-point cell sums, FP64 thermostat factor) with the cell-level
+Maxwell-Boltzmann thermostat at kT = 1 and 2000 chains of 50 beads (mass 5,
+harmonic bonds k = 1000, r0 = 0.5, 10 velocity-Verlet substeps per
+collision), alpha = 130 deg, dt = 0.1, grid shift every step, 500 steps.
+Synthetic, seeded inputs (uniform positions, zero-momentum Maxwell-Boltzmann
+velocities, random-walk chains).
 
 One JSON line on rank 0:
   value     particle-steps/s of the whole job, state resident in HBM, timed with
@@ -14,6 +17,9 @@ One JSON line on rank 0:
             get_state), wall clock
   roofline  dominant kernel: algorithmic bytes / its event-timed duration
   cpu_baseline  the CPU oracle, single thread, on a bounded sample
+  extra     (N = 1, default workload) the 10^7-particle SRD box, the 64-box
+            ensemble batched against per-box launches (a short run), and a
+            short served sweep below saturation with p50/p99 job latency
 --impl reference times the CPU oracle (the reference of this build) instead.
 Multi-GPU (torchrun): independent replica boxes per rank (weak scaling).
 """
@@ -44,6 +50,8 @@ FP64_PEAK_TFLOPS = 1.25          # GB300 nominal FP64 (non-tensor) rate
 # r + v dt 6, r - s 3.  The per-cell work (u, the axis) is not counted.
 FP64_FLOPS_PER_PARTICLE = 48
 METRIC = "MPCD particle-steps/s"
+# the 50M+ particle mixed-precision box: 7.8e7 particles, thermostat, solute
+DEFAULT_WORKLOAD = "srd-250c-rho5-mixed-solute"
 UNIT = "particle-steps/s"
 # kernels launched per step: the fused cell kernel and the record update; the
 # solute adds MD + bead grouping, 3 bead-scan phases and the bead scatter
@@ -254,7 +262,9 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="srd-100c-rho10-mixed")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra figures (10^7 box, batched ratio, served sweep)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jobs", type=int, default=None, help="served workload: number of jobs")
@@ -360,8 +370,10 @@ def main():
     traffic = kernel_traffic(kname, args.workload)
     roofline = {"bound": "hbm", "kernel": f"{kname} (collide t + stream/bin t+1)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
-                "alg_bytes_per_particle": step_bytes}
+                "frac": achieved / hbm_peak, "frac_of_8tbs": achieved / 8000.0,
+                "traffic": traffic, "peak_source": peak_src,
+                "alg_bytes_per_particle": step_bytes,
+                "kernel_ms": dom_ms, "particles": int(s.pos.shape[0])}
     if cfg["precision"] == "fp64":
         # The FP64 model is bound by the FP64 pipe, not by HBM: on GB300 FP64
         # runs at 1/64 of the FP32 rate.  Algorithmic FP64 flops per particle
@@ -371,7 +383,8 @@ def main():
         roofline = {"bound": "alu", "kernel": f"{kname} (collide t + stream/bin t+1)",
                     "achieved": flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": flops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                    "peak_source": "nominal: GB300 FP64 (non-tensor) rate from the "
+                                   "data sheet, not measured",
                     "alg_flops_per_particle": FP64_FLOPS_PER_PARTICLE,
                     "hbm_frac": achieved / hbm_peak}
     step_gbs = step_bytes * N * K / (ms * 1e-3) / 1e9 / world
@@ -416,6 +429,14 @@ def main():
     launches = per_step * K
     config["l2"] = (f"state {s.pos.shape[0] * 6 * es / 1e6:.0f} MB > 129 MB L2 (inputs larger "
                     "than L2; no flush)")
+    config["device_bytes"] = box.footprint_bytes()
+    config["bytes_per_particle"] = box.footprint_bytes() / N
+    box.close()
+
+    # ---- extra figures (N = 1, default workload) ----
+    extra = None
+    if world == 1 and not args.no_extra and args.workload == DEFAULT_WORKLOAD:
+        extra = run_extra(pkg, torch, stream, hbm_peak)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -423,11 +444,78 @@ def main():
                 "dtype": "f64" if cfg["precision"] == "fp64" else "f32+i64",
                 "data": "synthetic", "config": config, "clocks": clocks, "e2e": e2e,
                 "gpu_launches": launches, "roofline": roofline, "hbm_step": hbm_step,
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu, "extra": extra}
         print(json.dumps(line))
-    box.close()
     if dist:
         dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ extra figures
+def run_extra(pkg, torch, stream, hbm_peak):
+    """Short runs of the other measured forms, for the default line: the
+    10^7-particle SRD box (device-resident rate and the fused kernel's
+    roofline), the 64-box ensemble batched against per-box plain launches,
+    and the served workload at two arrival rates below saturation."""
+    out = {}
+    # 10^7-particle SRD box, mixed, no thermostat
+    name = "srd-100c-rho10-mixed"
+    cfg = workload_cfg(name)
+    s, _, _ = make_state(cfg)
+    box = pkg.Box(stream=stream.cuda_stream, **box_kwargs(cfg))
+    box.set_state(s.pos, s.vel)
+    box.step(10)
+    box.tune(2)
+    box.step(2)
+    torch.cuda.synchronize()
+    K = 500
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    box.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    phases = box.phase_times(50)
+    n = s.pos.shape[0]
+    gbs = 60 * n / (phases["fused_step"] * 1e-3) / 1e9
+    out[name] = {"particles": n, "steps": K, "ms_per_step": ms / K,
+                 "value": n * K / (ms * 1e-3), "unit": UNIT,
+                 "fused_kernel_ms": phases["fused_step"], "achieved_gbs": gbs,
+                 "frac": gbs / hbm_peak, "frac_of_8tbs": gbs / 8000.0,
+                 "bytes_per_particle": box.footprint_bytes() / n}
+    box.close()
+    del s
+    # 64-box ensemble: one batch against per-box plain launches
+    bcfg = workload_cfg("srd-batch64-mixed")
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    args = argparse.Namespace(workload="srd-batch64-mixed")
+    b = _run_batch(pkg, torch, stream, sampler, args, bcfg, 50, 5, 0, 1, None)
+    out["srd-batch64-mixed"] = {
+        "boxes": b["config"]["boxes"], "particles": b["config"]["particles"], "steps": 50,
+        "batched": b["value"], "per_box_plain_launches": b["per_box_plain_launches"]["value"],
+        "ratio_batched_over_per_box": b["per_box_plain_launches"]["ratio_batched_over_per_box"],
+        "unit": UNIT}
+    # served workload below saturation: two arrival rates, 60 jobs each
+    from paper_1801_10187_gb300 import serve
+    scfg = workload_cfg("srd-served-poisson")
+    free, _total = torch.cuda.mem_get_info()
+    sweep = []
+    for rate in (5.0, 10.0):
+        jobs = serve.poisson_jobs(60, rate, seed=scfg["jobs_seed"] + 200, l_min=scfg["l_min"],
+                                  l_max=scfg["l_max"], density=scfg["density"],
+                                  steps_min=scfg["steps_min"], steps_max=scfg["steps_max"],
+                                  alpha_deg=scfg["alpha_deg"])
+        srv = serve.Server(precision=scfg["precision"], max_bytes=int(free * 0.8),
+                           stream=stream.cuda_stream)
+        st = srv.run(jobs, realtime=True)
+        srv.close()
+        d = st.as_dict()
+        d["rate_jobs_per_s"] = rate
+        sweep.append(d)
+    out["srd-served-poisson"] = {"recipe": "serve.poisson_jobs, 60 jobs per rate: L "
+                                           "log-uniform [10,160], density 5, steps "
+                                           "U[100,5000], 130 deg, thermostat every other job",
+                                 "sweep": sweep}
+    return out
 
 
 # ------------------------------------------------------------------ batched / served

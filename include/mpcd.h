@@ -198,20 +198,25 @@ int mpcd_observables(mpcd_ctx* ctx, mpcd_obs* out);
 int mpcd_profile(mpcd_ctx* ctx, int32_t nbins, double* out);
 
 /* Allocation-free mpcd_profile, for callers that cannot allocate device
- * memory when they ask for a profile: code running while a stream is being
- * captured into a CUDA graph (device allocation is not allowed there), or a
- * service running inside a fixed, pre-reserved device-memory budget.  Same
- * result as mpcd_profile (nbins doubles, mean solvent v_x per z slab).  The
- * per-bin scratch is a static device array of 4096 bins (64 KiB) that every
- * GPU loading the library holds until the process exits; nbins outside
+ * memory when they ask for a profile: a service that runs inside a fixed,
+ * pre-reserved device-memory budget (every byte is handed out up front, so a
+ * library allocation could fail or push the process over its budget), or a
+ * job server that keeps nearly all of the GPU's memory filled with resident
+ * boxes, where an allocation at query time could fail with out-of-memory.
+ * Same result as mpcd_profile (nbins doubles, mean solvent v_x per z slab).
+ * The per-bin scratch is a static device array of 4096 bins (64 KiB) that
+ * every GPU loading the library holds until the process exits; nbins outside
  * [1, 4096] is rejected with MPCD_EINVAL.  The first call on a device looks
- * up that array's device address, so make the first call before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
- * (several threads, or contexts on different streams) race and must be
- * serialised by the caller.  Needs the box on the device already: after
- * set_state, call mpcd_step once (0 steps is enough), else MPCD_ESTATE.
- * Synchronises.  The paper has no counterpart: this is an allocation policy of
- * the library, not part of the method. */
+ * up that array's device address (cudaGetSymbolAddress, once per device), so
+ * make the first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents (each call clears the bins it uses):
+ * calls whose work overlaps on the GPU (several threads, or contexts on
+ * different streams) race and must be serialised by the caller.  Needs the
+ * box on the device already: after set_state, call mpcd_step once (0 steps
+ * is enough), else MPCD_ESTATE.  A pending collision is completed first.
+ * Synchronises the box's stream: it waits for the box's work and copies the
+ * result to the host.  The paper has no counterpart: this is an allocation
+ * policy of the library, not part of the method. */
 int mpcd_profile_noalloc(mpcd_ctx* ctx, int32_t nbins, double* out);
 
 /* Per-particle cell ids and per-cell member counts of the LAST completed

@@ -284,6 +284,10 @@ class Box:
         _check(lib().mpcd_profile_noalloc(self._ctx, int(nbins), _dptr(out)))
         return out
 
+    def footprint_bytes(self) -> int:
+        """Device bytes of this box's solvent arrays (mpcd_box_footprint)."""
+        return int(lib().mpcd_box_footprint(ctypes.byref(self.params), int(self.n_solvent)))
+
     def last_cells(self):
         cells = np.empty(self.n_solvent + self.n_solute, dtype=np.int32)
         counts = np.empty(self.num_cells, dtype=np.int32)

@@ -1,13 +1,15 @@
 """The allocation-free profile entry point, mpcd_profile_noalloc.
 
 It is for callers that cannot allocate device memory when they ask for the
-Poiseuille profile (code running while a stream is captured into a CUDA
-graph, services inside a fixed device-memory budget): it uses a static
-4096-bin device scratch array instead of allocating.  Checked here through the
-C ABI against mpcd_profile, the entry point that allocates its scratch, on two
-calls in a row (the shared array keeps the previous call's contents, so the
-second call shows it is cleared), within the tolerance of the other GPU tests.
-This file is collected last on purpose.
+Poiseuille profile (services inside a fixed, pre-reserved device-memory
+budget; job servers whose resident boxes fill the GPU's memory): it uses a
+static 4096-bin device scratch array instead of allocating.  Checked here
+through the C ABI against mpcd_profile, the entry point that allocates its
+scratch, on two calls in a row (the shared array keeps the previous call's
+contents, so the second call shows it is cleared), within the tolerance of
+the other GPU tests.  The first call comes straight after stepping, so it
+also completes the pending collision itself.  This file is collected last on
+purpose.
 """
 import numpy as np
 import pytest
@@ -32,9 +34,18 @@ def test_profile_noalloc_matches_profile_on_two_calls(precision):
                   body_force=(0.02, 0.0, 0.0), virt_density=10.0)
     box.set_state(s.pos, s.vel)
     box.step(20)
-    ref = box.profile(24)
+    # the collision of the last step is still pending: the allocation-free
+    # call completes it before it reads the state
     first = box.profile_noalloc(24)
+    ref = box.profile(24)
     second = box.profile_noalloc(24)
+    # a twin box stepped the same way, profiled by the allocating call alone
+    twin = pkg.Box(n=n, seed=17, precision=precision, thermostat=True, walls_z=True,
+                   body_force=(0.02, 0.0, 0.0), virt_density=10.0)
+    twin.set_state(s.pos, s.vel)
+    twin.step(20)
+    np.testing.assert_allclose(first, twin.profile(24), rtol=0, atol=TOL)
+    twin.close()
     np.testing.assert_allclose(first, ref, rtol=0, atol=TOL)
     np.testing.assert_allclose(second, ref, rtol=0, atol=TOL)
     # a smaller request after a larger one: nothing of the earlier call leaks in
