@@ -162,8 +162,10 @@ static float neg_log1m_f(uint32_t hi, uint32_t lo) {
   return -log_series_f(e);
 }
 
-static float xi_mixed(double H, double E);
-float oracle_xi_mixed(double ehat, double ek) { return xi_mixed(ehat, ek); }
+static float xi_mixed(double H, float Hf, double E, float Ef);
+float oracle_xi_mixed(double ehat, double ek) {
+  return xi_mixed(ehat, (float)ehat, ek, (float)ek);
+}
 void oracle_cos_sin_turn_f(uint32_t w, float* c, float* s) { cos_sin_turn_f(w, c, s); }
 float oracle_log_f(float x) { return log_series_f(x); }
 float oracle_neg_log1m_f(uint32_t hi, uint32_t lo) { return neg_log1m_f(hi, lo); }
@@ -220,10 +222,11 @@ void oracle_axis(uint64_t seed, uint64_t t, uint32_t cell, int32_t precision, do
 /* Marsaglia & Tsang (2000) with a Box-Muller normal (cosine branch).        */
 /* Attempt j uses counters (cell, 1+2j) and (cell, 2+2j).                     */
 /* ------------------------------------------------------------------------ */
-int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, double kT,
-                          int32_t precision, double* ehat) {
-  if (nc < 2) return -1;
-  if (precision == ORACLE_MIXED) {
+/* The mixed model's attempt loop: the accepted Marsaglia-Tsang pair (d, v),
+ * E^ = d v kT.  Returns 0, or -4 after 64 rejections. */
+static int32_t gamma_mixed_dv(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, float* dout,
+                              float* vout) {
+  {
     float kk = 1.5f * (float)(nc - 1);
     float d = kk - 1.0f / 3.0f;
     float c = 1.0f / sqrtf(9.0f * d);
@@ -246,18 +249,31 @@ int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, 
        * the acceptance region, so it accepts without the logarithms. */
       float x2 = x * x;
       if (U3 < 1.0f - 0.0331f * (x2 * x2)) {
-        *ehat = ((double)d * (double)v) * kT;
+        *dout = d;
+        *vout = v;
         return 0;
       }
       float lhs = log_series_f(U3);
       float rhs = 0.5f * x2 + d - d * v + d * log_series_f(v);
       int accept = lhs < rhs;
       if (accept) {
-        *ehat = ((double)d * (double)v) * kT;
+        *dout = d;
+        *vout = v;
         return 0;
       }
     }
     return -4;
+  }
+}
+
+int32_t oracle_gamma_draw(uint64_t seed, uint64_t t, uint32_t cell, int32_t nc, double kT,
+                          int32_t precision, double* ehat) {
+  if (nc < 2) return -1;
+  if (precision == ORACLE_MIXED) {
+    float d, v;
+    int32_t st = gamma_mixed_dv(seed, t, cell, nc, &d, &v);
+    if (st == 0) *ehat = ((double)d * (double)v) * kT;
+    return st;
   }
   double kk = 1.5 * (double)(nc - 1);
   double d = kk - 1.0 / 3.0;
@@ -831,16 +847,17 @@ static void rotate_f(const float n[3], float ca, float sa, float omc, const floa
 }
 
 /* Mixed model, Eq. (thermo): xi = sqrt(E^/E_k) to double accuracy, rounded
- * to float.  The float estimate y0 = sqrt(RN(E^)/RN(E_k)) (about 1e-7
- * relative) is refined by one Newton step in double,
+ * to float.  H, E: E^ and E_k in double; Hf, Ef: their float estimates
+ * (formed from the same exact quantities by float operations, see one_step).
+ * The float estimate y0 = sqrt(Hf / Ef) (about 1e-7 relative) is refined by
+ * one Newton step in double,
  *   y1 = y0 + (E^ - y0^2 E_k) / (2 y0 E_k),
  * the residual by one fused multiply-add (y0^2 is exact in double) and the
  * step's 1/(2 y0 E_k) in float: its rounding scales a correction of relative
  * size 1e-7, so y1 is within a few 1e-14 of the square root.  E^ = 0 (kT = 0)
  * gives xi = 0. */
-static float xi_mixed(double H, double E) {
-  const float Ef = (float)E;
-  const float y0 = sqrtf((float)H / Ef);
+static float xi_mixed(double H, float Hf, double E, float Ef) {
+  const float y0 = sqrtf(Hf / Ef);
   if (!(y0 > 0.0f)) return y0;
   const double r = fma(-((double)y0 * (double)y0), E, H);
   const float inv = 0.5f / (y0 * Ef);
@@ -882,6 +899,9 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
   const int32_t arith = mixed ? ORACLE_MIXED : ORACLE_FP64;
   const double m = p->mass, Mb = p->solute_mass;
   const double ca = cos(p->alpha), sa = sin(p->alpha), omc = 1.0 - ca;
+  /* mixed model: E_k = hm Es + 2^-33 Ex from the exact energy sums */
+  const double hm = 0.5 * m * 0x1p-32;
+  const float hmf = (float)hm;
   int32_t status = 0;
 
   /* Solute: MD substeps between collisions (Sec. 3.6, last paragraph). */
@@ -1103,14 +1123,25 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
        * double accuracy (xi_mixed), rounded to the float that scales the
        * float relative velocities. */
       double Ek;
-      if (mixed) Ek = fma(0x1p-33, (double)cb->Ex[c], (0.5 * m * 0x1p-32) * (double)cb->Es[c]);
+      if (mixed) Ek = fma(0x1p-33, (double)cb->Ex[c], hm * (double)cb->Es[c]);
       else Ek = cb->E[c];
       if (Ek > 0.0) {
-        double ehat;
-        int32_t st = oracle_gamma_draw(p->seed, t, (uint32_t)c, nc, p->kT, arith, &ehat);
-        if (st != 0) { status = st; continue; }
-        if (mixed) cb->xi[c] = (double)xi_mixed(ehat, Ek);
-        else cb->xi[c] = sqrt(ehat / Ek);
+        if (mixed) {
+          /* E^ = d v kT and E_k in double; their float estimates from the
+           * same factors in float */
+          float d, v;
+          int32_t st = gamma_mixed_dv(p->seed, t, (uint32_t)c, nc, &d, &v);
+          if (st != 0) { status = st; continue; }
+          const double H = ((double)d * (double)v) * p->kT;
+          const float Hf = (d * v) * (float)p->kT;
+          const float Ef = (float)cb->Es[c] * hmf + (float)cb->Ex[c] * 0x1p-33f;
+          cb->xi[c] = (double)xi_mixed(H, Hf, Ek, Ef);
+        } else {
+          double ehat;
+          int32_t st = oracle_gamma_draw(p->seed, t, (uint32_t)c, nc, p->kT, arith, &ehat);
+          if (st != 0) { status = st; continue; }
+          cb->xi[c] = sqrt(ehat / Ek);
+        }
       }
     }
   }

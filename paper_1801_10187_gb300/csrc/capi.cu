@@ -805,6 +805,8 @@ struct Engine {
       d.md_h = p.dt / (double)p.md_substeps;
       d.md_hh = (0.5 * d.md_h) / p.solute_mass;
     }
+    d.hm = 0.5 * p.mass * 0x1p-32;
+    d.hm_f = (float)d.hm;
     d.dt_f = (float)p.dt;
     d.kT_f = (float)p.kT;
     d.m_f = (float)p.mass;

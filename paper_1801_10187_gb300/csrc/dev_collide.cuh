@@ -235,27 +235,52 @@ __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, u
   n[2] = z;
 }
 
-// Mixed model, Eq. (thermo): xi = sqrt(E^/E_k) to double accuracy, rounded to
-// float.  The float estimate y0 = sqrt(RN(E^)/RN(E_k)) is refined by one
-// Newton step in double, y1 = y0 + (E^ - y0^2 E_k) / (2 y0 E_k): the residual
-// by one fused multiply-add (y0^2 is exact in double), the step's
-// 1/(2 y0 E_k) in float (its rounding scales a correction of relative size
-// 1e-7).  About a dozen FP64-pipe instructions per cell instead of the two
-// dozen of a double division and square root.  E^ = 0 gives xi = 0.
-__device__ __forceinline__ float xi_mixed(double H, double E) {
-  const float Ef = __double2float_rn(E);
-  const float y0 = sqrtf(__fdiv_rn(__double2float_rn(H), Ef));
-  if (!(y0 > 0.0f)) return y0;
-  const double r = __fma_rn(-__dmul_rn((double)y0, (double)y0), E, H);
-  const float inv = __fdiv_rn(0.5f, __fmul_rn(y0, Ef));
-  return __double2float_rn(__fma_rn(r, (double)inv, (double)y0));
+// Exact conversions to double on the integer pipe (the FP64 pipe of GB300
+// runs at about 1/64 of the FP32 rate and also executes the conversion
+// instructions): a float, and an integer 0 <= q < 2^53.  Other inputs (zero,
+// subnormal or non-finite floats; other integers) take the hardware
+// conversion, which gives the same value.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)f;
+  const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double ll2d_exact(long long q) {
+  if (q <= 0 || q >= (1LL << 53)) return __ll2double_rn(q);
+  const int lz = __clzll(q);  // the top bit of q at 63 - lz <= 52
+  const unsigned long long m = (unsigned long long)q << (lz - 11);
+  return __longlong_as_double((long long)(((unsigned long long)(1022 + 63 - lz) << 52) + m));
 }
 
-// E_k of the mixed model in double from the exact sums: solvent sum es of
+// Mixed model, Eq. (thermo): xi = sqrt(E^/E_k) to double accuracy, rounded to
+// float.  H, E: E^ and E_k in double; Hf, Ef: float estimates of them formed
+// by float operations from the same exact factors.  y0 = sqrt(Hf / Ef) is
+// refined by one Newton step in double, y1 = y0 + (E^ - y0^2 E_k) /
+// (2 y0 E_k): the residual by one fused multiply-add (y0^2 is exact in
+// double), the step's 1/(2 y0 E_k) in float (its rounding scales a
+// correction of relative size 1e-7).  With the factors converted on the
+// integer pipe, about eight FP64-pipe instructions per cell in all instead of
+// the two dozen of a double division and square root.  E^ = 0 gives xi = 0.
+__device__ __forceinline__ float xi_mixed(double H, float Hf, double E, float Ef) {
+  const float y0 = sqrtf(__fdiv_rn(Hf, Ef));
+  if (!(y0 > 0.0f)) return y0;
+  const double yd = f2d_exact(y0);
+  const double r = __fma_rn(-__dmul_rn(yd, yd), E, H);
+  const float inv = __fdiv_rn(0.5f, __fmul_rn(y0, Ef));
+  return __double2float_rn(__fma_rn(r, f2d_exact(inv), yd));
+}
+
+// E_k of the mixed model from the exact sums: solvent sum es of
 // rne(|v - u|^2 2^32) (mass factored out) and the beads' and virtual
-// particles' sum ex of rne(m |v - u|^2 2^32); m and 1/2 enter as exact scalings.
-__device__ __forceinline__ double mixed_energy(double m, long long es, long long ex) {
-  return __fma_rn(0x1p-33, __ll2double_rn(ex), __dmul_rn(0.5 * m * 0x1p-32, __ll2double_rn(es)));
+// particles' sum ex of rne(m |v - u|^2 2^32), E_k = hm es + 2^-33 ex with
+// hm = m 2^-33 (exact scalings), in double and, for the estimate, in float.
+__device__ __forceinline__ double mixed_energy(double hm, long long es, long long ex) {
+  return __fma_rn(0x1p-33, ll2d_exact(ex), __dmul_rn(hm, ll2d_exact(es)));
+}
+__device__ __forceinline__ float mixed_energy_f(float hm_f, long long es, long long ex) {
+  return __fadd_rn(__fmul_rn(i64_to_float(es), hm_f), __fmul_rn(i64_to_float(ex), 0x1p-33f));
 }
 
 // ---------------------------------------------------------------------------
@@ -266,11 +291,11 @@ __device__ __forceinline__ double mixed_energy(double m, long long es, long long
 // their low words are in block B = (cell, 2 + 2j).  gamma_draw_mixed, the
 // mixed model's sampler, decides every acceptance in float with the series
 // above (block B only for the far tail of the radius, see neg_log1m) and
-// forms E^ = (d v) kT in double from the float d and v; gamma_draw is the
-// FP64 sampler.  Both return false after 64 rejections.
+// returns the accepted d and v (E^ = d v kT); gamma_draw is the FP64 sampler.
+// Both return false after 64 rejections.
 // ---------------------------------------------------------------------------
 __device__ inline bool gamma_draw_mixed(const BoxDev& B, unsigned long long t, uint32_t cell,
-                                        int nc, double& ehat) {
+                                        int nc, float& dout, float& vout) {
   const float kk = 1.5f * small_to_float(nc - 1);
   const float d = kk - 1.0f / 3.0f;
   const float c = 1.0f / sqrtf(9.0f * d);
@@ -288,11 +313,35 @@ __device__ inline bool gamma_draw_mixed(const BoxDev& B, unsigned long long t, u
     bool accept = U3 < 1.0f - 0.0331f * (x2 * x2);
     if (!accept) accept = series_log(U3) < 0.5f * x2 + d - d * v + d * series_log(v);
     if (accept) {
-      ehat = __dmul_rn(__dmul_rn((double)d, (double)v), B.kT);
+      dout = d;
+      vout = v;
       return true;
     }
   }
   return false;
+}
+
+// Mixed model: the thermostat factor of a cell whose energy sums about u are
+// es (solvent) and ex (beads, virtual particles), Eq. thermo, from the
+// sampler's accepted pair (d, v), E^ = d v kT; d < 0 marks a sampler that gave
+// up.  xi is left at 1 when E_k = 0; false if E_k > 0 and there is no draw.
+__device__ __forceinline__ bool thermo_xi_from_draw(const BoxDev& B, float d, float v,
+                                                    long long es, long long ex, float& xi) {
+  const double E = mixed_energy(B.hm, es, ex);
+  if (!(E > 0.0)) return true;
+  if (d < 0.0f) return false;
+  const double H = __dmul_rn(__dmul_rn(f2d_exact(d), f2d_exact(v)), B.kT);
+  const float Hf = __fmul_rn(__fmul_rn(d, v), B.kT_f);
+  xi = xi_mixed(H, Hf, E, mixed_energy_f(B.hm_f, es, ex));
+  return true;
+}
+__device__ __forceinline__ bool thermo_xi_mixed(const BoxDev& B, unsigned long long t,
+                                                uint32_t cell, int nc, long long es, long long ex,
+                                                float& xi) {
+  if (!(mixed_energy(B.hm, es, ex) > 0.0)) return true;  // xi stays 1
+  float d, v;
+  if (!gamma_draw_mixed(B, t, cell, nc, d, v)) return false;
+  return thermo_xi_from_draw(B, d, v, es, ex, xi);
 }
 
 __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
@@ -451,7 +500,7 @@ template <> struct CellAcc<true> {
   }
   // E_k in double from the exact sums (the thermostat factor is FP64).
   __device__ __forceinline__ double energy(const BoxDev& B, bool) const {
-    return mixed_energy(B.m, es, ex);
+    return mixed_energy(B.hm, es, ex);
   }
   __device__ __forceinline__ void add_energy_partial(const CellAcc& o) { es += o.es; }
 };
@@ -585,15 +634,17 @@ __device__ __forceinline__ void cell_finish(const BoxDev& B, unsigned long long 
     // Eq. thermo: xi = sqrt(E^ / E_k), in FP64 in both models (the mixed
     // model rounds it to the float that scales its relative velocities)
     const int nc = a.ns + a.nb + a.nv;
-    const double Ek = a.energy(B, extra);
-    if (nc >= 2 && Ek > 0.0) {
-      double ehat;
-      bool ok;
-      if constexpr (MIXED) ok = gamma_draw_mixed(B, t, cell, nc, ehat);
-      else ok = gamma_draw(B, t, cell, nc, ehat);
-      if (!ok) atomicOr(err, ERR_GAMMA_CAP);
-      else if constexpr (MIXED) xi = xi_mixed(ehat, Ek);
-      else xi = sqrt(ehat / Ek);
+    if (nc >= 2) {
+      if constexpr (MIXED) {
+        if (!thermo_xi_mixed(B, t, cell, nc, a.es, a.ex, xi)) atomicOr(err, ERR_GAMMA_CAP);
+      } else {
+        const double Ek = a.energy(B, extra);
+        double ehat;
+        if (Ek > 0.0) {
+          if (gamma_draw(B, t, cell, nc, ehat)) xi = sqrt(ehat / Ek);
+          else atomicOr(err, ERR_GAMMA_CAP);
+        }
+      }
     }
   }
 #pragma unroll

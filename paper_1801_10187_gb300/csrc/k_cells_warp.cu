@@ -63,6 +63,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 struct WarpShared {
   float4 prm[2][32];               // (u, xi), (axis, 0) per cell
+  float2 gdv[32];                  // thermostat: accepted Gamma pair (d, v); d < 0: none
   int h[3][32];                    // sum over the cell of H (momentum); h[0]: energy
   int l[3][32];                    // sum of L
   int offs[33];                    // first member of each cell; offs[32] = members
@@ -325,6 +326,53 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       }
     };
 
+    // Solute beads join their cell's collision with mass M (Sec. 3.6).  The
+    // 32 cells of the warp are one bead group; its beads are handled one per
+    // lane (grouped copies of cell and velocity): first their count and exact
+    // int64 momentum per cell, into shared sums.
+    int gb0 = 0, gnb = 0, nb = 0;
+    auto for_beads = [&](auto&& f) {  // f(slot in the group order, local cell)
+      for (int j0 = 0; j0 < gnb; j0 += 32) {
+        const int j = gb0 + j0 + lane;
+        if (j0 + lane < gnb) f(j, B.bgc[j] - c0);
+      }
+    };
+    if (BEADS && MODE != MODE_P) {
+      const int g = c0 / B.tc;
+      gb0 = (int)B.bstart[g];
+      gnb = (int)B.bstart[g + 1] - gb0;
+      if (gnb > 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) BS.X[q][lane] = 0ull;
+        BS.E[lane] = 0ull;
+        BS.nb[lane] = 0;
+        __syncwarp();
+        for_beads([&](int j, int lc) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            atomicAdd(&BS.X[q][lc],
+                      (unsigned long long)__double2ll_rn((B.Mb * B.bgv[3 * j + q]) * 4294967296.0));
+          atomicAdd(&BS.nb[lc], 1);
+        });
+        __syncwarp();
+        nb = BS.nb[lane];
+      }
+    }
+    // The per-cell draws of the step need only the member count, so they
+    // come before the sums (less state is live here): the axis (Sec. 3.6)
+    // and, with the thermostat, the accepted Gamma pair (d, v), E^ = d v kT.
+    if (MODE != MODE_P && !AT && (n > 0 || nb > 0)) {
+      float ax[3];
+      axis_of(B, t, (uint32_t)cell, ax);
+      W.prm[1][lane] = make_float4(ax[0], ax[1], ax[2], 0.0f);
+      if (THERMO) {
+        float d = -1.0f, v = 0.0f;
+        if ((int)n + nb >= 2 && !gamma_draw_mixed(B, t, (uint32_t)cell, (int)n + nb, d, v))
+          d = -1.0f;
+        W.gdv[lane] = make_float2(d, v);
+      }
+    }
+
     if (MODE != MODE_P) {
       // ---- pass 1: exact momentum sums per cell (Sec. 3.5) ----
 #pragma unroll
@@ -418,41 +466,11 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       const bool exact64 = __any_sync(FULL, slow);  // a velocity of 1024 or more
       const bool exact64_d = AT && __any_sync(FULL, slow_d);
 
-      // ---- per cell: u (Sec. 3.5), then the energy about u, axis and xi ----
-      // Solute beads join their cell's collision with mass M (Sec. 3.6).  The
-      // 32 cells of the warp are one bead group; its beads are handled one per
-      // lane (grouped copies of cell and velocity), adding exact int64
-      // momentum to their cell's shared sums.
-      int gb0 = 0, gnb = 0, nb = 0;
+      // ---- per cell: u (Sec. 3.5), then the energy about u and xi ----
       long long X[3] = {0, 0, 0};
-      auto for_beads = [&](auto&& f) {  // f(slot in the group order, local cell)
-        for (int j0 = 0; j0 < gnb; j0 += 32) {
-          const int j = gb0 + j0 + lane;
-          if (j0 + lane < gnb) f(j, B.bgc[j] - c0);
-        }
-      };
-      if (BEADS) {
-        const int g = c0 / B.tc;
-        gb0 = (int)B.bstart[g];
-        gnb = (int)B.bstart[g + 1] - gb0;
-        if (gnb > 0) {
+      if (BEADS && gnb > 0) {
 #pragma unroll
-          for (int q = 0; q < 3; ++q) BS.X[q][lane] = 0ull;
-          BS.E[lane] = 0ull;
-          BS.nb[lane] = 0;
-          __syncwarp();
-          for_beads([&](int j, int lc) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-              atomicAdd(&BS.X[q][lc],
-                        (unsigned long long)__double2ll_rn((B.Mb * B.bgv[3 * j + q]) * 4294967296.0));
-            atomicAdd(&BS.nb[lc], 1);
-          });
-          __syncwarp();
-          nb = BS.nb[lane];
-#pragma unroll
-          for (int q = 0; q < 3; ++q) X[q] = (long long)BS.X[q][lane];
-        }
+        for (int q = 0; q < 3; ++q) X[q] = (long long)BS.X[q][lane];
       }
       const bool occupied = n > 0 || nb > 0;
       float u[3] = {0.0f, 0.0f, 0.0f};
@@ -604,21 +622,13 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
           // xi = sqrt(E^/E_k) in FP64 from the exact sums, rounded to float
           const long long Etot =
               exact64_e ? Es : (long long)W.h[0][lane] * 1048576LL + (long long)W.l[0][lane] + Es;
-          const double Ek = mixed_energy(B.m, Etot, Ex);
-          const int nc = (int)n + nb;
-          if (nc >= 2 && Ek > 0.0) {
-            double ehat;
-            if (gamma_draw_mixed(B, t, (uint32_t)cell, nc, ehat)) xi = xi_mixed(ehat, Ek);
-            else atomicOr(err, ERR_GAMMA_CAP);
+          if ((int)n + nb >= 2) {
+            const float2 dv = W.gdv[lane];
+            if (!thermo_xi_from_draw(B, dv.x, dv.y, Etot, Ex, xi)) atomicOr(err, ERR_GAMMA_CAP);
           }
         }
       }
-      if (occupied && !AT) {
-        float ax[3];
-        axis_of(B, t, (uint32_t)cell, ax);  // Sec. 3.6
-        W.prm[0][lane] = make_float4(u[0], u[1], u[2], xi);
-        W.prm[1][lane] = make_float4(ax[0], ax[1], ax[2], 0.0f);
-      }
+      if (occupied && !AT) W.prm[0][lane] = make_float4(u[0], u[1], u[2], xi);  // axis: prm[1]
       __syncwarp();
       if (BEADS && !AT && gnb > 0) {  // collide the beads with their cell's parameters
         for_beads([&](int j, int lc) {
