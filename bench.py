@@ -511,10 +511,21 @@ def run_extra(pkg, torch, stream, hbm_peak):
         d = st.as_dict()
         d["rate_jobs_per_s"] = rate
         sweep.append(d)
+    # the same 60 jobs all due at once (closed loop): the server saturated,
+    # its capacity beside the batched ensemble's
+    jobs = serve.poisson_jobs(60, 10.0, seed=scfg["jobs_seed"] + 200, l_min=scfg["l_min"],
+                              l_max=scfg["l_max"], density=scfg["density"],
+                              steps_min=scfg["steps_min"], steps_max=scfg["steps_max"],
+                              alpha_deg=scfg["alpha_deg"])
+    srv = serve.Server(precision=scfg["precision"], max_bytes=int(free * 0.8),
+                       stream=stream.cuda_stream)
+    st = srv.run(jobs, realtime=False)
+    srv.close()
+    saturated = st.as_dict()
     out["srd-served-poisson"] = {"recipe": "serve.poisson_jobs, 60 jobs per rate: L "
                                            "log-uniform [10,160], density 5, steps "
                                            "U[100,5000], 130 deg, thermostat every other job",
-                                 "sweep": sweep}
+                                 "sweep": sweep, "saturated_closed_loop": saturated}
     return out
 
 
