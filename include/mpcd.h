@@ -169,17 +169,20 @@ int mpcd_set_state_thermal(mpcd_ctx* ctx, int64_t n_solvent, uint64_t init_seed,
 int mpcd_step(mpcd_ctx* ctx, int64_t nsteps);
 
 /* Launch tuner (the paper tunes its kernels' launch parameters on real steps
- * at run time, Sec. 3.5 and Sec. 4): each candidate grid of the fused step
- * kernel -- 1 up to the occupancy limit of blocks per SM, and one block per
- * 256-cell span -- runs steps_per_candidate real steps, timed with CUDA
- * events; the fastest is kept for later steps.  The simulation advances by
- * *steps_taken steps (one more when the first step must stream and bin).
- * Results do not depend on the grid (mixed model bit for bit; FP64 to
- * rounding).  Outputs may be NULL: *blocks_per_sm (-1 = one block per span),
- * *ms_per_step of the winner.  Synchronises.  Errors: EINVAL, ESTATE, ECUDA,
- * EDEVICE. */
+ * at run time, Sec. 3.5 and Sec. 4): each candidate of the fused step kernel
+ * -- its grid (1 up to the occupancy limit of blocks per SM, and one block per
+ * 256-cell span) times, for mixed boxes with the SRD rule and no angular
+ * correction, the depth of pass 2 (2, 3 or 4 windows of 32 members whose
+ * record loads and slot requests are in flight together) -- runs
+ * steps_per_candidate real steps, timed with CUDA events; the fastest is kept
+ * for later steps.  The simulation advances by *steps_taken steps (one more
+ * when the first step must stream and bin).  Results do not depend on the
+ * candidate (mixed model bit for bit; FP64 to rounding).  Outputs may be
+ * NULL: *blocks_per_sm (-1 = one block per span), *ms_per_step of the winner,
+ * *pass2_chunk (windows per chunk).  Synchronises.  Errors: EINVAL, ESTATE,
+ * ECUDA, EDEVICE. */
 int mpcd_tune(mpcd_ctx* ctx, int64_t steps_per_candidate, int32_t* blocks_per_sm,
-              double* ms_per_step, int64_t* steps_taken);
+              double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk);
 
 /* Copy the state out in input (tag) order; arrays as for set_state (solute
  * arrays may be NULL).  Synchronises.  Errors: ESTATE, ECUDA, EDEVICE. */
@@ -272,9 +275,9 @@ int mpcd_batch_add_thermal(mpcd_batch* b, const mpcd_params* params, int64_t n_s
 /* Advance every resident box by nsteps.  Asynchronous like mpcd_step. */
 int mpcd_batch_step(mpcd_batch* b, int64_t nsteps);
 
-/* mpcd_tune for every resident box together (one grid choice for the batch). */
+/* mpcd_tune for every resident box together (one choice for the batch). */
 int mpcd_batch_tune(mpcd_batch* b, int64_t steps_per_candidate, int32_t* blocks_per_sm,
-                    double* ms_per_step, int64_t* steps_taken);
+                    double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk);
 
 /* Copy one box's state out (tag order).  Synchronises. */
 int mpcd_batch_get_state(mpcd_batch* b, int32_t slot, double* pos, double* vel,

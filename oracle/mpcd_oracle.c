@@ -877,8 +877,8 @@ typedef struct {
   double* E;      /* FP64 mode: kinetic energy about u */
   int64_t* Qs;    /* MIXED: solvent sum of rne(v 2^32) (3 per cell) */
   int64_t* Qx;    /* MIXED: beads/virtual sum of rne(m v 2^32) (3 per cell) */
-  int64_t* Es;    /* MIXED: solvent sum of rne(|v-u|^2 2^32) */
-  int64_t* Ex;    /* MIXED: beads/virtual sum of rne(m |v-u|^2 2^32) */
+  __int128* S2;   /* MIXED: solvent sum of V^2 over members and components, V = rne(v 2^32) */
+  int64_t* Kx;    /* MIXED: beads/virtual sum of rne(m |v|^2 2^32) */
   double* u;      /* centre-of-mass velocity (3 per cell) */
   double* axis;   /* rotation axis (3 per cell) */
   double* xi;     /* thermostat scale factor */
@@ -887,6 +887,36 @@ typedef struct {
   int64_t* Qdx;   /* MIXED, Andersen rule: beads sum of rne(M dv 2^32) */
   double* dbar;   /* Andersen rule: mass-weighted mean random velocity (3 per cell) */
 } cellbuf;
+
+/* Mixed model, Eq. (thermo) with Sec. 3.5's one pass: E_k = K - |P|^2 / (2 Mt)
+ * from the cell's exact sums, returned multiplied by the cell mass Mt (set in
+ * *Mt).  A cell of solvent only (n members, momentum sums Q of V = rne(v 2^32),
+ * second moment S2 = sum V^2): E_k Mt = (m^2 / 2) 2^-64 (n S2 - |Q|^2), the
+ * integer exact (Cauchy-Schwarz keeps it >= 0) and rounded once.  With beads
+ * or virtual particles (momentum sums X of rne(m v 2^32), kinetic sums Kx of
+ * rne(m |v|^2 2^32)): K = m S2 2^-64 + Kx 2^-32, P = (m Q + X) 2^-32 and
+ * E_k Mt = (Mt K - |P|^2) / 2 in double. */
+static double mixed_ek_mt(const oracle_params* p, const cellbuf* cb, int64_t c, double hm2,
+                          double* Mt) {
+  const double m = p->mass;
+  const int32_t ns = cb->nsol[c], nbd = cb->nbead[c], nv = cb->nvirt[c];
+  const int64_t* Q = &cb->Qs[3 * c];
+  if (nbd == 0 && nv == 0) {
+    const __int128 D = (__int128)ns * cb->S2[c] -
+                       ((__int128)Q[0] * Q[0] + (__int128)Q[1] * Q[1] + (__int128)Q[2] * Q[2]);
+    *Mt = m * (double)ns;
+    return hm2 * (double)D;
+  }
+  const int64_t* X = &cb->Qx[3 * c];
+  *Mt = (m * (double)ns + p->solute_mass * (double)nbd) + m * (double)nv;
+  const double K = ((m * (double)cb->S2[c]) * 0x1p-64) + (double)cb->Kx[c] * 0x1p-32;
+  double P2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double P = (m * (double)Q[k] + (double)X[k]) * 0x1p-32;
+    P2 = P2 + P * P;
+  }
+  return 0.5 * (*Mt * K - P2);
+}
 
 static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* vel, int64_t nb,
                         double* spos, double* svel, uint64_t t, int32_t* cellid, cellbuf* cb,
@@ -899,9 +929,8 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
   const int32_t arith = mixed ? ORACLE_MIXED : ORACLE_FP64;
   const double m = p->mass, Mb = p->solute_mass;
   const double ca = cos(p->alpha), sa = sin(p->alpha), omc = 1.0 - ca;
-  /* mixed model: E_k = hm Es + 2^-33 Ex from the exact energy sums */
-  const double hm = 0.5 * m * 0x1p-32;
-  const float hmf = (float)hm;
+  /* mixed model: E_k Mt = hm2 (n S2 - |Q|^2) for a cell of solvent only */
+  const double hm2 = ((0.5 * m) * m) * 0x1p-64;
   int32_t status = 0;
 
   /* Solute: MD substeps between collisions (Sec. 3.6, last paragraph). */
@@ -944,20 +973,29 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
   if (mixed) {
     memset(cb->Qs, 0, sizeof(int64_t) * 3 * ncells);
     memset(cb->Qx, 0, sizeof(int64_t) * 3 * ncells);
-    memset(cb->Es, 0, sizeof(int64_t) * ncells);
-    memset(cb->Ex, 0, sizeof(int64_t) * ncells);
+    memset(cb->S2, 0, sizeof(__int128) * ncells);
+    memset(cb->Kx, 0, sizeof(int64_t) * ncells);
   } else {
     memset(cb->M, 0, sizeof(double) * ncells);
     memset(cb->P, 0, sizeof(double) * 3 * ncells);
     memset(cb->E, 0, sizeof(double) * ncells);
   }
+  /* Mixed model: the same pass accumulates the kinetic energy as the exact
+   * integer sum of V^2 (Sec. 3.5: momentum, mass and kinetic energy in one
+   * pass), so E_k = K - |P|^2 / 2M carries no rounding before the final
+   * conversion. */
   for (int64_t i = 0; i < n; ++i) {
     int32_t c = cellid[i];
     cb->cnt[c] += 1;
     cb->nsol[c] += 1;
     for (int k = 0; k < 3; ++k) {
-      if (mixed) cb->Qs[3 * c + k] += llrint(vel[3 * i + k] * 0x1p32);
-      else cb->P[3 * c + k] += m * vel[3 * i + k];
+      if (mixed) {
+        const int64_t V = llrint(vel[3 * i + k] * 0x1p32);
+        cb->Qs[3 * c + k] += V;
+        cb->S2[c] += (__int128)V * V;
+      } else {
+        cb->P[3 * c + k] += m * vel[3 * i + k];
+      }
     }
     if (!mixed) cb->M[c] += m;
   }
@@ -968,6 +1006,10 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     for (int k = 0; k < 3; ++k) {
       if (mixed) cb->Qx[3 * c + k] += llrint((Mb * svel[3 * b + k]) * 0x1p32);
       else cb->P[3 * c + k] += Mb * svel[3 * b + k];
+    }
+    if (mixed) {
+      const double* w = &svel[3 * b];
+      cb->Kx[c] += llrint((Mb * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2])) * 0x1p32);
     }
     if (!mixed) cb->M[c] += Mb;
   }
@@ -986,6 +1028,7 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
           if (mixed) cb->Qx[3 * c + k] += llrint((m * vv[k]) * 0x1p32);
           else cb->P[3 * c + k] += m * vv[k];
         }
+        if (mixed) cb->Kx[c] += llrint((m * (vv[0] * vv[0] + vv[1] * vv[1] + vv[2] * vv[2])) * 0x1p32);
         if (!mixed) cb->M[c] += m;
       }
     }
@@ -1073,29 +1116,22 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     return status;
   }
 
-  /* Thermostat: kinetic energy about u, Eq. (thermo). */
-  if (p->thermostat) {
+  /* Thermostat, FP64 model: kinetic energy about u, Eq. (thermo), in a second
+   * pass (the mixed model has it from the exact sums above). */
+  if (p->thermostat && !mixed) {
     for (int64_t i = 0; i < n; ++i) {
       int32_t c = cellid[i];
-      if (mixed) {
-        float d[3];
-        for (int k = 0; k < 3; ++k) d[k] = (float)vel[3 * i + k] - (float)cb->u[3 * c + k];
-        float e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        cb->Es[c] += llrint((double)e * 0x1p32);
-      } else {
-        double d[3];
-        for (int k = 0; k < 3; ++k) d[k] = vel[3 * i + k] - cb->u[3 * c + k];
-        double e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        cb->E[c] += (0.5 * m) * e;
-      }
+      double d[3];
+      for (int k = 0; k < 3; ++k) d[k] = vel[3 * i + k] - cb->u[3 * c + k];
+      double e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      cb->E[c] += (0.5 * m) * e;
     }
     for (int64_t b = 0; b < nb; ++b) {
       int32_t c = cellid[n + b];
       double d[3];
       for (int k = 0; k < 3; ++k) d[k] = svel[3 * b + k] - cb->u[3 * c + k];
       double e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      if (mixed) cb->Ex[c] += llrint((Mb * e) * 0x1p32);
-      else cb->E[c] += (0.5 * Mb) * e;
+      cb->E[c] += (0.5 * Mb) * e;
     }
     if (p->walls_z) {
       for (int64_t c = 0; c < ncells; ++c) {
@@ -1104,8 +1140,7 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
           virtual_velocity(p, t, (uint32_t)c, q, vv);
           for (int k = 0; k < 3; ++k) d[k] = vv[k] - cb->u[3 * c + k];
           double e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-          if (mixed) cb->Ex[c] += llrint((m * e) * 0x1p32);
-          else cb->E[c] += (0.5 * m) * e;
+          cb->E[c] += (0.5 * m) * e;
         }
       }
     }
@@ -1118,24 +1153,19 @@ static int32_t one_step(const oracle_params* p, int64_t n, double* pos, double* 
     oracle_axis(p->seed, t, (uint32_t)c, arith, &cb->axis[3 * c]);
     int32_t nc = cb->cnt[c] + cb->nvirt[c];
     if (p->thermostat && nc >= 2) {
-      /* Mixed model: E_k in double from the exact fixed-point sums (mass and
-       * the factor 1/2 applied as exact scalings), and xi = sqrt(E^/E_k) to
-       * double accuracy (xi_mixed), rounded to the float that scales the
-       * float relative velocities. */
-      double Ek;
-      if (mixed) Ek = fma(0x1p-33, (double)cb->Ex[c], hm * (double)cb->Es[c]);
+      /* Mixed model: E_k Mt (E_k times the cell's mass) from the exact sums,
+       * and xi = sqrt(E^ Mt / (E_k Mt)) to double accuracy (xi_mixed),
+       * rounded to the float that scales the float relative velocities. */
+      double Ek, Mt = 1.0;
+      if (mixed) Ek = mixed_ek_mt(p, cb, c, hm2, &Mt);
       else Ek = cb->E[c];
       if (Ek > 0.0) {
         if (mixed) {
-          /* E^ = d v kT and E_k in double; their float estimates from the
-           * same factors in float */
           float d, v;
           int32_t st = gamma_mixed_dv(p->seed, t, (uint32_t)c, nc, &d, &v);
           if (st != 0) { status = st; continue; }
-          const double H = ((double)d * (double)v) * p->kT;
-          const float Hf = (d * v) * (float)p->kT;
-          const float Ef = (float)cb->Es[c] * hmf + (float)cb->Ex[c] * 0x1p-33f;
-          cb->xi[c] = (double)xi_mixed(H, Hf, Ek, Ef);
+          const double H = (((double)d * (double)v) * p->kT) * Mt;
+          cb->xi[c] = (double)xi_mixed(H, (float)H, Ek, (float)Ek);
         } else {
           double ehat;
           int32_t st = oracle_gamma_draw(p->seed, t, (uint32_t)c, nc, p->kT, arith, &ehat);
@@ -1226,8 +1256,8 @@ int32_t oracle_step(const oracle_params* p, int64_t n, double* pos, double* vel,
   cb.E = (double*)calloc((size_t)ncells, sizeof(double));
   cb.Qs = (int64_t*)calloc((size_t)ncells * 3, sizeof(int64_t));
   cb.Qx = (int64_t*)calloc((size_t)ncells * 3, sizeof(int64_t));
-  cb.Es = (int64_t*)calloc((size_t)ncells, sizeof(int64_t));
-  cb.Ex = (int64_t*)calloc((size_t)ncells, sizeof(int64_t));
+  cb.S2 = (__int128*)calloc((size_t)ncells, sizeof(__int128));
+  cb.Kx = (int64_t*)calloc((size_t)ncells, sizeof(int64_t));
   cb.u = (double*)calloc((size_t)ncells * 3, sizeof(double));
   cb.axis = (double*)calloc((size_t)ncells * 3, sizeof(double));
   cb.xi = (double*)calloc((size_t)ncells, sizeof(double));
@@ -1245,7 +1275,7 @@ int32_t oracle_step(const oracle_params* p, int64_t n, double* pos, double* vel,
   free(cellid);
   free(cb.cnt); free(cb.nsol); free(cb.nbead); free(cb.nvirt);
   free(cb.M); free(cb.P); free(cb.E);
-  free(cb.Qs); free(cb.Qx); free(cb.Es); free(cb.Ex);
+  free(cb.Qs); free(cb.Qx); free(cb.S2); free(cb.Kx);
   free(cb.u); free(cb.axis); free(cb.xi);
   free(cb.D); free(cb.Qd); free(cb.Qdx); free(cb.dbar);
   return st;

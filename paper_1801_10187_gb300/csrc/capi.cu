@@ -303,6 +303,10 @@ struct Engine {
   bool any_beads = false;
   int wca_substeps = 0;  // most MD substeps of a box with the WCA repulsion (0: none)
   int cells_bps[3][NVAR] = {};
+  // F mode of the mixed SRD warp variants: blocks per SM for each pass-2 chunk
+  // depth (2, 3, 4), and the depth in use (a launch-tuner choice)
+  int bps_chunk[5][NVAR] = {};
+  int tuned_chunk = 3;
 
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // MODE_P, MODE_F, MODE_C
   bool tables_ok = false;
@@ -326,17 +330,25 @@ struct Engine {
         if ((v & 4) && ang)  // warp-spread angular correction: mixed SRD without beads
           cells_bps[m][v] = (mixed && !(v & (8 | 16)))
                                 ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, false, false,
-                                                           true, m)
+                                                           true, m, 3)
                                 : 1;
         else if ((v & 4) && !(at && (v & 1)))
           cells_bps[m][v] =
-              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, false, m)
+              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, false, m, 3)
                     : cells_warpd_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, m);
         else if (!(v & 4))
           cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
         else
           cells_bps[m][v] = 1;
         if (cells_bps[m][v] < 1) cells_bps[m][v] = 1;
+      }
+    for (int v = 0; v < NVAR; ++v)
+      for (int ch = 2; ch <= 4; ++ch) {
+        bps_chunk[ch][v] = cells_bps[MODE_F][v];
+        if (chunk_tunable(v))
+          bps_chunk[ch][v] = std::max(1, cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0,
+                                                                  (v & 8) != 0, false, false,
+                                                                  MODE_F, ch));
       }
     CUDA_TRY((cudaError_t)md_bin_prepare());
     CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
@@ -519,6 +531,9 @@ struct Engine {
     return MPCD_OK;
   }
 
+  // variants whose F-mode launch takes the tuned pass-2 chunk depth
+  bool chunk_tunable(int v) const { return mixed && (v & 4) && !(v & (16 | 32)); }
+
   int grid_for(int n, int per_sm) const {
     const int g = nsm * per_sm;
     return n < g ? std::max(n, 1) : g;
@@ -529,8 +544,8 @@ struct Engine {
   int tuned_grid = 0;
   int grid_of(int v, int mode) const {
     if (mode == MODE_F && tuned_grid == -1) return std::max(n_spans[v], 1);
-    const int bps = (mode == MODE_F && tuned_grid > 0) ? std::min(tuned_grid, cells_bps[mode][v])
-                                                      : cells_bps[mode][v];
+    const int limit = (mode == MODE_F) ? bps_chunk[tuned_chunk][v] : cells_bps[mode][v];
+    const int bps = (mode == MODE_F && tuned_grid > 0) ? std::min(tuned_grid, limit) : limit;
     return grid_for(n_spans[v], bps);
   }
 
@@ -541,7 +556,7 @@ struct Engine {
       const bool at = (v & 16) != 0;
       if ((v & 4) && mixed)
         launch_cells_warp((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, (v & 32) != 0, mode,
-                          d_boxes, d_spans[v], n_spans[v], grid, d_err, stream);
+                          d_boxes, d_spans[v], n_spans[v], grid, tuned_chunk, d_err, stream);
       else if (v & 4)
         launch_cells_warpd((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, mode, d_boxes,
                            d_spans[v], n_spans[v], grid, d_err, stream);
@@ -624,12 +639,15 @@ struct Engine {
   }
 
   // Launch tuner.  The paper tunes its kernels' launch parameters at run time
-  // on real steps (Sec. 3.5, Sec. 4).  Here each candidate grid of the fused
-  // pass (1 .. occupancy-limit blocks per SM, and one block per span) runs
-  // `reps` real steps, timed with CUDA events on the stream; the fastest is
-  // kept and the step graph re-captured.  Results do not depend on the grid:
-  // the mixed model's cell sums are exact, the FP64 ones differ at rounding.
-  int tune(int64_t reps, int32_t* chosen, double* best_ms, int64_t* steps_taken) {
+  // on real steps (Sec. 3.5, Sec. 4).  Here each candidate of the fused pass
+  // -- grid (1 .. occupancy-limit blocks per SM, and one block per span)
+  // times pass-2 chunk depth (2, 3, 4 windows of members in flight, for the
+  // mixed SRD variants) -- runs `reps` real steps, timed with CUDA events on
+  // the stream; the fastest is kept and the step graph re-captured.  Results
+  // do not depend on the candidate: the mixed model's cell sums are exact,
+  // the FP64 ones differ at rounding.
+  int tune(int64_t reps, int32_t* chosen, double* best_ms, int64_t* steps_taken,
+           int32_t* chosen_chunk) {
     if (reps < 1) return fail(MPCD_EINVAL, "steps per candidate < 1");
     int rc = ensure_tables();
     if (rc) return rc;
@@ -643,37 +661,47 @@ struct Engine {
       pending = true;
       taken += 1;
     }
-    int maxbps = 1;
+    bool any_chunk = false;
     for (int v = 0; v < NVAR; ++v)
-      if (n_spans[v] > 0) maxbps = std::max(maxbps, cells_bps[MODE_F][v]);
-    std::vector<int> cand;
-    for (int k = 1; k <= maxbps; ++k) cand.push_back(k);
-    cand.push_back(-1);
+      if (n_spans[v] > 0 && chunk_tunable(v)) any_chunk = true;
+    std::vector<int> chunks = any_chunk ? std::vector<int>{2, 3, 4} : std::vector<int>{3};
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     double best = 1e30;
-    int best_c = 0;
-    for (int c : cand) {
-      tuned_grid = c;
-      CUDA_TRY(cudaEventRecord(e0, stream));
-      for (int64_t r = 0; r < reps; ++r) enqueue_pass(MODE_F);
-      CUDA_TRY(cudaEventRecord(e1, stream));
-      CUDA_TRY(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-      taken += reps;
-      if (ms / (double)reps < best) {
-        best = ms / (double)reps;
-        best_c = c;
+    int best_c = 0, best_ch = 3;
+    for (int ch : chunks) {
+      tuned_chunk = ch;
+      int maxbps = 1;
+      for (int v = 0; v < NVAR; ++v)
+        if (n_spans[v] > 0) maxbps = std::max(maxbps, bps_chunk[ch][v]);
+      std::vector<int> cand;
+      for (int k = 1; k <= maxbps; ++k) cand.push_back(k);
+      cand.push_back(-1);
+      for (int c : cand) {
+        tuned_grid = c;
+        CUDA_TRY(cudaEventRecord(e0, stream));
+        for (int64_t r = 0; r < reps; ++r) enqueue_pass(MODE_F);
+        CUDA_TRY(cudaEventRecord(e1, stream));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        taken += reps;
+        if (ms / (double)reps < best) {
+          best = ms / (double)reps;
+          best_c = c;
+          best_ch = ch;
+        }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     tuned_grid = best_c;
+    tuned_chunk = best_ch;
     drop_graphs();
     CUDA_TRY(cudaGetLastError());
     if (chosen) *chosen = best_c;
+    if (chosen_chunk) *chosen_chunk = best_ch;
     if (best_ms) *best_ms = best;
     if (steps_taken) *steps_taken = taken;
     return check_err();
@@ -805,8 +833,7 @@ struct Engine {
       d.md_h = p.dt / (double)p.md_substeps;
       d.md_hh = (0.5 * d.md_h) / p.solute_mass;
     }
-    d.hm = 0.5 * p.mass * 0x1p-32;
-    d.hm_f = (float)d.hm;
+    d.hm2 = ((0.5 * p.mass) * p.mass) * 0x1p-64;
     d.dt_f = (float)p.dt;
     d.kT_f = (float)p.kT;
     d.m_f = (float)p.mass;
@@ -1105,11 +1132,11 @@ int mpcd_step(mpcd_ctx* ctx, int64_t nsteps) {
 }
 
 int mpcd_tune(mpcd_ctx* ctx, int64_t steps_per_candidate, int32_t* blocks_per_sm,
-              double* ms_per_step, int64_t* steps_taken) {
+              double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk) {
   g_last_error.clear();
   if (!ctx) return fail(MPCD_EINVAL, "ctx is NULL");
   if (!ctx->box->has_state) return fail(MPCD_ESTATE, "no state set");
-  return ctx->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken);
+  return ctx->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken, pass2_chunk);
 }
 
 int mpcd_get_state(mpcd_ctx* ctx, double* pos, double* vel, double* solute_pos, double* solute_vel,
@@ -1336,10 +1363,10 @@ int mpcd_batch_step(mpcd_batch* bt, int64_t nsteps) {
 }
 
 int mpcd_batch_tune(mpcd_batch* bt, int64_t steps_per_candidate, int32_t* blocks_per_sm,
-                    double* ms_per_step, int64_t* steps_taken) {
+                    double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk) {
   g_last_error.clear();
   if (!bt) return fail(MPCD_EINVAL, "batch is NULL");
-  return bt->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken);
+  return bt->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken, pass2_chunk);
 }
 
 int mpcd_batch_get_state(mpcd_batch* bt, int32_t slot, double* pos, double* vel, uint64_t* step) {

@@ -272,15 +272,55 @@ __device__ __forceinline__ float xi_mixed(double H, float Hf, double E, float Ef
   return __double2float_rn(__fma_rn(r, f2d_exact(inv), yd));
 }
 
-// E_k of the mixed model from the exact sums: solvent sum es of
-// rne(|v - u|^2 2^32) (mass factored out) and the beads' and virtual
-// particles' sum ex of rne(m |v - u|^2 2^32), E_k = hm es + 2^-33 ex with
-// hm = m 2^-33 (exact scalings), in double and, for the estimate, in float.
-__device__ __forceinline__ double mixed_energy(double hm, long long es, long long ex) {
-  return __fma_rn(0x1p-33, ll2d_exact(ex), __dmul_rn(hm, ll2d_exact(es)));
+// The nearest double (ties to even) of an unsigned 128-bit integer, on the
+// integer pipe.
+__device__ __forceinline__ double u128_to_double(unsigned __int128 x) {
+  const unsigned long long hi = (unsigned long long)(x >> 64), lo = (unsigned long long)x;
+  if (hi == 0ull && lo < (1ull << 53)) return ll2d_exact((long long)lo);
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  const int p = 127 - lz;  // the top bit, >= 53 here
+  const int sh = p - 52;
+  unsigned __int128 m = x >> sh;
+  const unsigned __int128 rem = x & (((unsigned __int128)1 << sh) - 1);
+  const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+  if (rem > half || (rem == half && (m & 1))) m += 1;
+  int e = p;
+  if (m >> 53) {
+    m >>= 1;
+    e += 1;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) |
+                                          ((unsigned long long)m & ((1ull << 52) - 1ull))));
 }
-__device__ __forceinline__ float mixed_energy_f(float hm_f, long long es, long long ex) {
-  return __fadd_rn(__fmul_rn(i64_to_float(es), hm_f), __fmul_rn(i64_to_float(ex), 0x1p-33f));
+
+// Mixed model, Eq. (thermo) with the one pass of Sec. 3.5 (momentum, mass and
+// kinetic energy together): E_k = K - |P|^2 / (2 Mt) from the cell's exact
+// sums, returned times the cell mass Mt (also returned).  Solvent only (ns
+// members, momentum sums Q of V = rne(v 2^32), second moment S2 = sum V^2):
+// E_k Mt = (m^2 / 2) 2^-64 (ns S2 - |Q|^2), the integer exact (>= 0 by
+// Cauchy-Schwarz) and rounded once.  With beads or virtual particles
+// (momentum sums X of rne(m v 2^32), kinetic sums Kx of rne(m |v|^2 2^32)):
+// K = m S2 2^-64 + Kx 2^-32, P = (m Q + X) 2^-32, E_k Mt = (Mt K - |P|^2) / 2
+// in double.
+__device__ __forceinline__ double mixed_ek_mt(const BoxDev& B, int ns, int nbd, int nv,
+                                              const long long Q[3], __int128 S2,
+                                              const long long X[3], long long Kx, double& Mt) {
+  const double m = B.m;
+  if (nbd == 0 && nv == 0) {
+    const __int128 D = (__int128)ns * S2 - ((__int128)Q[0] * Q[0] + (__int128)Q[1] * Q[1] +
+                                            (__int128)Q[2] * Q[2]);
+    Mt = m * ll2d_exact(ns);
+    return B.hm2 * u128_to_double((unsigned __int128)D);
+  }
+  Mt = (m * ll2d_exact(ns) + B.Mb * ll2d_exact(nbd)) + m * ll2d_exact(nv);
+  const double K = ((m * u128_to_double((unsigned __int128)S2)) * 0x1p-64) + ll2d_exact(Kx) * 0x1p-32;
+  double P2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double P = (m * ll2d_exact(Q[k]) + ll2d_exact(X[k])) * 0x1p-32;
+    P2 = P2 + P * P;
+  }
+  return 0.5 * (Mt * K - P2);
 }
 
 // ---------------------------------------------------------------------------
@@ -321,27 +361,17 @@ __device__ inline bool gamma_draw_mixed(const BoxDev& B, unsigned long long t, u
   return false;
 }
 
-// Mixed model: the thermostat factor of a cell whose energy sums about u are
-// es (solvent) and ex (beads, virtual particles), Eq. thermo, from the
-// sampler's accepted pair (d, v), E^ = d v kT; d < 0 marks a sampler that gave
-// up.  xi is left at 1 when E_k = 0; false if E_k > 0 and there is no draw.
-__device__ __forceinline__ bool thermo_xi_from_draw(const BoxDev& B, float d, float v,
-                                                    long long es, long long ex, float& xi) {
-  const double E = mixed_energy(B.hm, es, ex);
-  if (!(E > 0.0)) return true;
+// Mixed model: the thermostat factor of a cell with E_k Mt = Ep and mass Mt
+// (mixed_ek_mt), Eq. thermo, from the sampler's accepted pair (d, v),
+// E^ = d v kT; d < 0 marks a sampler that gave up.  xi is left at 1 when
+// E_k = 0; false if E_k > 0 and there is no draw.
+__device__ __forceinline__ bool thermo_xi_from_draw(const BoxDev& B, float d, float v, double Ep,
+                                                    double Mt, float& xi) {
+  if (!(Ep > 0.0)) return true;
   if (d < 0.0f) return false;
-  const double H = __dmul_rn(__dmul_rn(f2d_exact(d), f2d_exact(v)), B.kT);
-  const float Hf = __fmul_rn(__fmul_rn(d, v), B.kT_f);
-  xi = xi_mixed(H, Hf, E, mixed_energy_f(B.hm_f, es, ex));
+  const double H = ((f2d_exact(d) * f2d_exact(v)) * B.kT) * Mt;
+  xi = xi_mixed(H, __double2float_rn(H), Ep, __double2float_rn(Ep));
   return true;
-}
-__device__ __forceinline__ bool thermo_xi_mixed(const BoxDev& B, unsigned long long t,
-                                                uint32_t cell, int nc, long long es, long long ex,
-                                                float& xi) {
-  if (!(mixed_energy(B.hm, es, ex) > 0.0)) return true;  // xi stays 1
-  float d, v;
-  if (!gamma_draw_mixed(B, t, cell, nc, d, v)) return false;
-  return thermo_xi_from_draw(B, d, v, es, ex, xi);
 }
 
 __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_t cell, int nc,
@@ -450,16 +480,22 @@ template <bool MIXED> struct CellAcc;
 
 template <> struct CellAcc<true> {
   long long q[3] = {0, 0, 0}, x[3] = {0, 0, 0};
-  long long es = 0, ex = 0;
+  __int128 s2 = 0;  // sum of V^2, V = rne(v 2^32), over members and components
+  long long kx = 0;  // extras: sum of rne(m |v|^2 2^32)
   int ns = 0, nb = 0, nv = 0;
   __device__ __forceinline__ void add_solvent(const BoxDev&, const float v[3]) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) q[k] += fix32_rne(v[k]);
+    for (int k = 0; k < 3; ++k) {
+      const long long V = fix32_rne(v[k]);
+      q[k] += V;
+      s2 += (__int128)V * V;
+    }
     ns += 1;
   }
   __device__ __forceinline__ void add_extra(double mass, const double v[3], bool bead) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) x[k] += __double2ll_rn((mass * v[k]) * 4294967296.0);
+    kx += __double2ll_rn((mass * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])) * 4294967296.0);
     if (bead) nb += 1;
     else nv += 1;
   }
@@ -469,8 +505,8 @@ template <> struct CellAcc<true> {
       q[k] += o.q[k];
       x[k] += o.x[k];
     }
-    es += o.es;
-    ex += o.ex;
+    s2 += o.s2;
+    kx += o.kx;
     ns += o.ns;
     nb += o.nb;
     nv += o.nv;
@@ -487,22 +523,10 @@ template <> struct CellAcc<true> {
       u[k] = (P * 0x1p-32f) / M;
     }
   }
-  __device__ __forceinline__ void add_solvent_energy(const BoxDev&, const float v[3],
-                                                     const float u[3]) {
-    const float d0 = v[0] - u[0], d1 = v[1] - u[1], d2 = v[2] - u[2];
-    const float e = d0 * d0 + d1 * d1 + d2 * d2;
-    es += fix32_rne(e);
+  // E_k times the cell mass, and the mass (the thermostat factor is FP64)
+  __device__ __forceinline__ double ek_mt(const BoxDev& B, double& Mt) const {
+    return mixed_ek_mt(B, ns, nb, nv, q, s2, x, kx, Mt);
   }
-  __device__ __forceinline__ void add_extra_energy(double mass, const double v[3], const float u[3]) {
-    const double d0 = v[0] - (double)u[0], d1 = v[1] - (double)u[1], d2 = v[2] - (double)u[2];
-    const double e = d0 * d0 + d1 * d1 + d2 * d2;
-    ex += __double2ll_rn((mass * e) * 4294967296.0);
-  }
-  // E_k in double from the exact sums (the thermostat factor is FP64).
-  __device__ __forceinline__ double energy(const BoxDev& B, bool) const {
-    return mixed_energy(B.hm, es, ex);
-  }
-  __device__ __forceinline__ void add_energy_partial(const CellAcc& o) { es += o.es; }
 };
 
 template <> struct CellAcc<false> {
@@ -617,18 +641,20 @@ __device__ __forceinline__ void cell_finish(const BoxDev& B, unsigned long long 
   axis_of(B, t, cell, n);
   T xi = (T)1;
   if (thermo) {
-    if (extra) {
-      for (int j = 0; j < nbt; ++j) {
-        int b;
-        if (bead_in(j, b)) {
-          const double vb[3] = {B.svel[3 * b], B.svel[3 * b + 1], B.svel[3 * b + 2]};
-          a.add_extra_energy(B.Mb, vb, u);
+    if constexpr (!MIXED) {  // the FP64 model's energy about u of the extras
+      if (extra) {
+        for (int j = 0; j < nbt; ++j) {
+          int b;
+          if (bead_in(j, b)) {
+            const double vb[3] = {B.svel[3 * b], B.svel[3 * b + 1], B.svel[3 * b + 2]};
+            a.add_extra_energy(B.Mb, vb, u);
+          }
         }
-      }
-      for (int q = 0; q < a.nv; ++q) {
-        double vv[3];
-        virtual_velocity(B, t, cell, q, vv);
-        a.add_extra_energy(B.m, vv, u);
+        for (int q = 0; q < a.nv; ++q) {
+          double vv[3];
+          virtual_velocity(B, t, cell, q, vv);
+          a.add_extra_energy(B.m, vv, u);
+        }
       }
     }
     // Eq. thermo: xi = sqrt(E^ / E_k), in FP64 in both models (the mixed
@@ -636,7 +662,11 @@ __device__ __forceinline__ void cell_finish(const BoxDev& B, unsigned long long 
     const int nc = a.ns + a.nb + a.nv;
     if (nc >= 2) {
       if constexpr (MIXED) {
-        if (!thermo_xi_mixed(B, t, cell, nc, a.es, a.ex, xi)) atomicOr(err, ERR_GAMMA_CAP);
+        double Mt;
+        const double Ep = a.ek_mt(B, Mt);
+        float d = -1.0f, v = 0.0f;
+        if (Ep > 0.0 && !gamma_draw_mixed(B, t, cell, nc, d, v)) d = -1.0f;
+        if (!thermo_xi_from_draw(B, d, v, Ep, Mt, xi)) atomicOr(err, ERR_GAMMA_CAP);
       } else {
         const double Ek = a.energy(B, extra);
         double ehat;

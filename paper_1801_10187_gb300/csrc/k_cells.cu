@@ -184,20 +184,24 @@ __global__ void __launch_bounds__(BLOCK) k_cells(const BoxDev* __restrict__ boxe
       if (has_ovf)
         for (uint32_t j = 0; j < novf; ++j)
           if (ovf_cell[j] == (uint32_t)cell) add_member(ovf + j);
+      // the FP64 model's energy about u (the mixed model has E_k from the
+      // exact sums of the first pass)
       auto solvent_energy = [&](const T u[3], CellAcc<MIXED>& acc) {
+        if constexpr (!MIXED) {
 #pragma unroll 4
-        for (int k = 0; k < nrow; ++k) {
-          T w[3];
-          load_v(row + k, w);
-          acc.add_solvent_energy(B, w, u);
+          for (int k = 0; k < nrow; ++k) {
+            T w[3];
+            load_v(row + k, w);
+            acc.add_solvent_energy(B, w, u);
+          }
+          if (has_ovf)
+            for (uint32_t j = 0; j < novf; ++j)
+              if (ovf_cell[j] == (uint32_t)cell) {
+                T w[3];
+                load_v(ovf + j, w);
+                acc.add_solvent_energy(B, w, u);
+              }
         }
-        if (has_ovf)
-          for (uint32_t j = 0; j < novf; ++j)
-            if (ovf_cell[j] == (uint32_t)cell) {
-              T w[3];
-              load_v(ovf + j, w);
-              acc.add_solvent_energy(B, w, u);
-            }
       };
       const double sz = EXTRA ? (double)sSz * 0x1p-32 : 0.0;
       T u[3];

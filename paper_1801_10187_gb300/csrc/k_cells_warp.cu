@@ -15,9 +15,11 @@
 //            roundings, summed in registers while the cell stays the same
 //            and added to the cell's shared sums by one atomic per part when
 //            it changes.  The sums are exact, so u is the one of any order.
-//   cell     lane c turns the sums of cell c into u, draws the axis (and with
-//            the thermostat, after the same kind of pass for the energy about
-//            u, the factor xi) and leaves them in shared memory
+//   cell     lane c turns the sums of cell c into u and, with the thermostat,
+//            into E_k (one pass, Sec. 3.5: pass 1 also sums the exact second
+//            moment of the split velocities) and the factor xi; the axis and
+//            the Gamma pair were drawn before pass 1 (they need only the
+//            member count).  u, xi and the axis go to shared memory
 //   pass 2   members in order across the lanes, in chunks of three windows:
 //            the chunk's records are copied into shared memory asynchronously
 //            (all in flight at once), each is collided with its cell's
@@ -53,7 +55,7 @@ constexpr int WARPS = BLOCK / 32;
 constexpr int MAP_MEMBERS = 640;  // members per warp with a byte owner map
 constexpr int STAGE = 256;        // member velocities staged per block of pass 1
 constexpr int STAGE_PAD = STAGE + STAGE / 32;
-constexpr int CHUNK = 3;          // windows of 32 members per chunk of pass 2
+constexpr int CHUNK = 3;          // windows of 32 members per chunk of pass 2 (default)
 
 // The wait for all of this thread's outstanding asynchronous copies (16-byte
 // global -> shared copies that bypass L1, issued below with an L2 policy).
@@ -61,22 +63,32 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// CH: windows of 32 members per chunk of pass 2 (the launch tuner picks 2, 3
+// or 4 for the F mode of the SRD variants; 3 elsewhere).
+template <int CH>
 struct WarpShared {
   float4 prm[2][32];               // (u, xi), (axis, 0) per cell
   float2 gdv[32];                  // thermostat: accepted Gamma pair (d, v); d < 0: none
-  int h[3][32];                    // sum over the cell of H (momentum); h[0]: energy
+  int h[3][32];                    // sum over the cell of H (momentum)
   int l[3][32];                    // sum of L
   int offs[33];                    // first member of each cell; offs[32] = members
   int pad_[3];
   unsigned char map[MAP_MEMBERS];  // owner lane of each member
   union {
     float sv[3][STAGE_PAD];        // pass 1: staged velocities (index j + j / 32)
-    float4 buf[CHUNK][2][32];      // pass 2: records of one chunk (two halves)
+    float4 buf[CH][2][32];         // pass 2: records of one chunk (two halves)
   };
 };
 
+// Thermostat variants: the exact second moment of each cell's split
+// velocities, sum over members and components of H^2, H L and L^2 (V = H 2^20
+// + L, so sum V^2 = 2^40 sum H^2 + 2^21 sum H L + sum L^2).
+struct ThermoShared {
+  unsigned long long hh[32], hl[32], ll[32];
+};
+
 // Per-cell bead accumulators of one warp (bead variants only): exact int64
-// momentum and energy sums and the bead count of each of the 32 cells.
+// momentum and kinetic-energy sums and the bead count of each of the 32 cells.
 struct BeadShared {
   unsigned long long X[3][32];
   unsigned long long E[32];
@@ -102,7 +114,8 @@ constexpr int DV_CAP_BEADS = 320;  // with the bead accumulators (two blocks per
 // Shared memory of one block: the span parameters, then one area per warp;
 // kept under 48 KB so that four blocks (the register limit) fit on an SM with
 // room left for L1.
-constexpr size_t WARP_SMEM = sizeof(WarpShared);
+template <int CH>
+constexpr size_t WARP_SMEM = sizeof(WarpShared<CH>);
 
 // Per-span parameters shared by the block.
 struct SpanParams {
@@ -119,8 +132,8 @@ struct SpanParams {
   int ovf_cap, pad;
 };
 constexpr size_t SPAN_SMEM = (sizeof(SpanParams) + 15) & ~(size_t)15;
-constexpr size_t BLOCK_SMEM = SPAN_SMEM + WARPS * WARP_SMEM;
-constexpr size_t BLOCK_SMEM_BEADS = BLOCK_SMEM + WARPS * sizeof(BeadShared);
+template <int CH>
+constexpr size_t BLOCK_SMEM = SPAN_SMEM + WARPS * WARP_SMEM<CH>;
 
 // Angular-momentum correction (SRD without beads): the float
 // frame of the collision step's shift (per block), and per warp the staged
@@ -140,10 +153,13 @@ struct AngWarp {
   float4 om[32];  // (omega, 0)
 };
 
-__host__ __device__ constexpr size_t block_smem(bool beads, bool at, bool ang = false) {
-  return BLOCK_SMEM + (beads ? WARPS * sizeof(BeadShared) : 0) +
+template <int CH = CHUNK>
+__host__ __device__ constexpr size_t block_smem(bool beads, bool at, bool ang = false,
+                                                bool thermo = false) {
+  return BLOCK_SMEM<CH> + (beads ? WARPS * sizeof(BeadShared) : 0) +
          (at ? WARPS * (beads ? sizeof(ATShared<DV_CAP_BEADS>) : sizeof(ATShared<DV_CAP>)) : 0) +
-         (ang ? sizeof(AngBlock) + WARPS * sizeof(AngWarp) : 0);
+         (ang ? sizeof(AngBlock) + WARPS * sizeof(AngWarp) : 0) +
+         (thermo ? WARPS * sizeof(ThermoShared) : 0);
 }
 
 }  // namespace
@@ -156,7 +172,7 @@ __host__ __device__ constexpr size_t block_smem(bool beads, bool at, bool ang = 
 // ANG adds the angular-momentum correction to SRD, with or without the
 // thermostat (then BEADS and AT are false); its shared memory allows two
 // blocks per SM.
-template <bool THERMO, int MODE, bool FORCE, bool BEADS, bool AT, bool ANG>
+template <bool THERMO, int MODE, bool FORCE, bool BEADS, bool AT, bool ANG, int CH = CHUNK>
 __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 3 : 4)) k_cells_warp(const BoxDev* __restrict__ boxes,
                                                          const int2* __restrict__ spans,
                                                          int nspans, int* err) {
@@ -164,13 +180,14 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
   extern __shared__ __align__(16) unsigned char smem_[];
   SpanParams& sp_ = *reinterpret_cast<SpanParams*>(smem_);
   const int lane = threadIdx.x & 31;
-  WarpShared& W =
-      reinterpret_cast<WarpShared*>(smem_ + SPAN_SMEM)[threadIdx.x >> 5];
-  BeadShared& BS = reinterpret_cast<BeadShared*>(smem_ + BLOCK_SMEM)[threadIdx.x >> 5];
+  WarpShared<CH>& W =
+      reinterpret_cast<WarpShared<CH>*>(smem_ + SPAN_SMEM)[threadIdx.x >> 5];
+  BeadShared& BS = reinterpret_cast<BeadShared*>(smem_ + BLOCK_SMEM<CH>)[threadIdx.x >> 5];
   constexpr int DVC = BEADS ? DV_CAP_BEADS : DV_CAP;
-  ATShared<DVC>& AS = reinterpret_cast<ATShared<DVC>*>(smem_ + block_smem(BEADS, false))[threadIdx.x >> 5];
-  AngBlock& AB = *reinterpret_cast<AngBlock*>(smem_ + block_smem(BEADS, AT));
-  AngWarp& AG = reinterpret_cast<AngWarp*>(smem_ + block_smem(BEADS, AT) + sizeof(AngBlock))[threadIdx.x >> 5];
+  ATShared<DVC>& AS = reinterpret_cast<ATShared<DVC>*>(smem_ + block_smem<CH>(BEADS, false))[threadIdx.x >> 5];
+  AngBlock& AB = *reinterpret_cast<AngBlock*>(smem_ + block_smem<CH>(BEADS, AT));
+  AngWarp& AG = reinterpret_cast<AngWarp*>(smem_ + block_smem<CH>(BEADS, AT) + sizeof(AngBlock))[threadIdx.x >> 5];
+  ThermoShared& TS = reinterpret_cast<ThermoShared*>(smem_ + block_smem<CH>(BEADS, AT, ANG))[threadIdx.x >> 5];
   const SpanParams& H = sp_;
   int box_of_params = -1;  // the span parameters depend on the box only
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
@@ -215,6 +232,13 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
     const int cur = B.cur;
     const int K = H.K;
     const uint32_t n = valid ? B.cnt[cur][cell] : 0u;
+    // the bead group's bounds, loaded together with the row counts
+    int gb0 = 0, gb1 = 0;
+    if (BEADS && MODE != MODE_P) {
+      const int g = c0 / B.tc;
+      gb0 = (int)B.bstart[g];
+      gb1 = (int)B.bstart[g + 1];
+    }
     if (MODE != MODE_C && n) B.cnt[cur][cell] = 0u;  // this set is written two steps on
     const int nrow = (int)n < K ? (int)n : K;
     const bool has_ovf = (int)n > K;
@@ -330,7 +354,8 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
     // 32 cells of the warp are one bead group; its beads are handled one per
     // lane (grouped copies of cell and velocity): first their count and exact
     // int64 momentum per cell, into shared sums.
-    int gb0 = 0, gnb = 0, nb = 0;
+    const int gnb = gb1 - gb0;
+    int nb = 0;
     auto for_beads = [&](auto&& f) {  // f(slot in the group order, local cell)
       for (int j0 = 0; j0 < gnb; j0 += 32) {
         const int j = gb0 + j0 + lane;
@@ -338,9 +363,6 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       }
     };
     if (BEADS && MODE != MODE_P) {
-      const int g = c0 / B.tc;
-      gb0 = (int)B.bstart[g];
-      gnb = (int)B.bstart[g + 1] - gb0;
       if (gnb > 0) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) BS.X[q][lane] = 0ull;
@@ -348,10 +370,13 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
         BS.nb[lane] = 0;
         __syncwarp();
         for_beads([&](int j, int lc) {
-#pragma unroll
-          for (int q = 0; q < 3; ++q)
-            atomicAdd(&BS.X[q][lc],
-                      (unsigned long long)__double2ll_rn((B.Mb * B.bgv[3 * j + q]) * 4294967296.0));
+          const double w0 = B.bgv[3 * j], w1 = B.bgv[3 * j + 1], w2 = B.bgv[3 * j + 2];
+          atomicAdd(&BS.X[0][lc], (unsigned long long)__double2ll_rn((B.Mb * w0) * 4294967296.0));
+          atomicAdd(&BS.X[1][lc], (unsigned long long)__double2ll_rn((B.Mb * w1) * 4294967296.0));
+          atomicAdd(&BS.X[2][lc], (unsigned long long)__double2ll_rn((B.Mb * w2) * 4294967296.0));
+          if (THERMO)  // kinetic term of the one-pass energy (Sec. 3.5)
+            atomicAdd(&BS.E[lc], (unsigned long long)__double2ll_rn(
+                                     (B.Mb * (w0 * w0 + w1 * w1 + w2 * w2)) * 4294967296.0));
           atomicAdd(&BS.nb[lc], 1);
         });
         __syncwarp();
@@ -388,6 +413,11 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
           AG.ql[q][lane] = 0;
         }
       }
+      if (THERMO) {
+        TS.hh[lane] = 0ull;
+        TS.hl[lane] = 0ull;
+        TS.ll[lane] = 0ull;
+      }
       __syncwarp();
       bool slow = false, slow_d = false;
       for (int sbase = 0; sbase < N; sbase += STAGE) {
@@ -396,6 +426,7 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
         int Hs[3] = {0, 0, 0}, Ls[3] = {0, 0, 0};
         int Hd[3] = {0, 0, 0}, Ld[3] = {0, 0, 0};
         int Hq[3] = {0, 0, 0}, Lq[3] = {0, 0, 0};
+        long long Shh = 0, Shl = 0, Sll = 0;  // thermostat: second moment
         share(sbase, cnt, [&](int o, int js, bool last) {
           if (ANG) {  // |position in the cell frame| < 2: the split never fails
 #pragma unroll
@@ -416,6 +447,11 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
             }
             Hs[q] += h;
             Ls[q] += l;
+            if (THERMO) {  // Sec. 3.5: the kinetic energy in the same pass, exactly
+              Shh += (long long)h * h;
+              Shl += (long long)h * l;
+              Sll += (long long)l * l;
+            }
           }
           if (AT) {  // Eq. at: this member's random velocity, summed the same way
             float dv[3];
@@ -440,6 +476,14 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
             }
           }
           if (last) {
+            if (THERMO) {
+              atomicAdd(&TS.hh[o], (unsigned long long)Shh);
+              atomicAdd(&TS.hl[o], (unsigned long long)Shl);
+              atomicAdd(&TS.ll[o], (unsigned long long)Sll);
+              Shh = 0;
+              Shl = 0;
+              Sll = 0;
+            }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
               atomicAdd(&W.h[q][o], Hs[q]);
@@ -466,7 +510,7 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       const bool exact64 = __any_sync(FULL, slow);  // a velocity of 1024 or more
       const bool exact64_d = AT && __any_sync(FULL, slow_d);
 
-      // ---- per cell: u (Sec. 3.5), then the energy about u and xi ----
+      // ---- per cell: u (Sec. 3.5), then E_k and xi ----
       long long X[3] = {0, 0, 0};
       if (BEADS && gnb > 0) {
 #pragma unroll
@@ -474,22 +518,29 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       }
       const bool occupied = n > 0 || nb > 0;
       float u[3] = {0.0f, 0.0f, 0.0f};
+      long long Q[3] = {0, 0, 0};  // exact path: this cell's sums of rne(v 2^32)
+      __int128 S2x = 0;            // and of their squares (thermostat)
       if (occupied) {
-        long long Q[3] = {0, 0, 0};
+        auto add_v = [&](const float w[3]) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const long long V = fix32_rne(w[q]);
+            Q[q] += V;
+            if (THERMO) S2x += (__int128)V * V;
+          }
+        };
         if (exact64)
           for (int k = 0; k < nrow; ++k) {
             float w[3];
             load_v(rows + (size_t)lane * K + k, w);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) Q[q] += fix32_rne(w[q]);
+            add_v(w);
           }
         if (has_ovf)
           for (uint32_t j = 0; j < novf; ++j)
             if (ovf_cell[j] == (uint32_t)cell) {
               float w[3];
               load_v(ovf + j, w);
-#pragma unroll
-              for (int q = 0; q < 3; ++q) Q[q] += fix32_rne(w[q]);
+              add_v(w);
             }
         float M = H.m * small_to_float((int)n);
         if (BEADS) M = M + (small_to_float(nb) * B.Mb_f + 0.0f * H.m);
@@ -563,70 +614,24 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
         __syncwarp();
       }
       float xi = 1.0f;
-      if (THERMO) {
-        W.h[0][lane] = 0;
-        W.l[0][lane] = 0;
-        __syncwarp();
-        if (BEADS && gnb > 0) {  // bead energies about their cell's u
-          for_beads([&](int j, int lc) {
-            const float4 uo = W.prm[0][lc];
-            const double d0 = B.bgv[3 * j] - (double)uo.x, d1 = B.bgv[3 * j + 1] - (double)uo.y,
-                         d2 = B.bgv[3 * j + 2] - (double)uo.z;
-            atomicAdd(&BS.E[lc], (unsigned long long)__double2ll_rn(
-                                     (B.Mb * (d0 * d0 + d1 * d1 + d2 * d2)) * 4294967296.0));
-          });
-          __syncwarp();
-        }
-        bool slow_e = false;
-        for (int sbase = 0; sbase < N; sbase += STAGE) {
-          const int cnt = min(STAGE, N - sbase);
-          if (N > STAGE) stage(sbase, cnt);  // else still staged from pass 1
-          int He = 0, Le = 0;
-          share(sbase, cnt, [&](int o, int js, bool last) {
-            const float4 uo = W.prm[0][o];
-            const float d0 = W.sv[0][js] - uo.x, d1 = W.sv[1][js] - uo.y, d2 = W.sv[2][js] - uo.z;
-            const float en = d0 * d0 + d1 * d1 + d2 * d2;
-            int h, l;
-            if (!split32(en, h, l)) {
-              slow_e = true;
-              h = 0;
-              l = 0;
-            }
-            He += h;
-            Le += l;
-            if (last) {
-              atomicAdd(&W.h[0][o], He);
-              atomicAdd(&W.l[0][o], Le);
-              He = 0;
-              Le = 0;
-            }
-          });
-          __syncwarp();
-        }
-        const bool exact64_e = __any_sync(FULL, slow_e);
-        if (occupied) {
-          long long Es = 0, Ex = 0;
-          auto add_energy = [&](const R* p) {
-            float w[3];
-            load_v(p, w);
-            const float d0 = w[0] - u[0], d1 = w[1] - u[1], d2 = w[2] - u[2];
-            Es += fix32_rne(d0 * d0 + d1 * d1 + d2 * d2);
-          };
-          if (exact64_e)
-            for (int k = 0; k < nrow; ++k) add_energy(rows + (size_t)lane * K + k);
-          if (has_ovf)
-            for (uint32_t j = 0; j < novf; ++j)
-              if (ovf_cell[j] == (uint32_t)cell) add_energy(ovf + j);
-          if (BEADS && gnb > 0) Ex = (long long)BS.E[lane];
-          // Eq. thermo: E_k about u, E^ ~ Gamma(3(N_c-1)/2, kT), and
-          // xi = sqrt(E^/E_k) in FP64 from the exact sums, rounded to float
-          const long long Etot =
-              exact64_e ? Es : (long long)W.h[0][lane] * 1048576LL + (long long)W.l[0][lane] + Es;
-          if ((int)n + nb >= 2) {
-            const float2 dv = W.gdv[lane];
-            if (!thermo_xi_from_draw(B, dv.x, dv.y, Etot, Ex, xi)) atomicOr(err, ERR_GAMMA_CAP);
-          }
-        }
+      if (THERMO && occupied && (int)n + nb >= 2) {
+        // Eq. thermo with the one pass of Sec. 3.5: E_k from the cell's exact
+        // sums (momentum, second moment; beads' momentum and kinetic term),
+        // xi = sqrt(E^/E_k) in FP64 from the Gamma pair drawn before pass 1
+        long long Qt[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          Qt[q] = exact64 ? Q[q] : (long long)W.h[q][lane] * 1048576LL + (long long)W.l[q][lane] + Q[q];
+        const __int128 S2 =
+            exact64 ? S2x
+                    : ((__int128)(long long)TS.hh[lane] << 40) +
+                          ((__int128)(long long)TS.hl[lane] << 21) + (__int128)(long long)TS.ll[lane] +
+                          S2x;
+        const long long Kx = (BEADS && gnb > 0) ? (long long)BS.E[lane] : 0ll;
+        double Mt;
+        const double Ep = mixed_ek_mt(B, (int)n, nb, 0, Qt, S2, X, Kx, Mt);
+        const float2 dv = W.gdv[lane];
+        if (!thermo_xi_from_draw(B, dv.x, dv.y, Ep, Mt, xi)) atomicOr(err, ERR_GAMMA_CAP);
       }
       if (occupied && !AT) W.prm[0][lane] = make_float4(u[0], u[1], u[2], xi);  // axis: prm[1]
       __syncwarp();
@@ -872,15 +877,15 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
         }
       }
     };
-    // Chunks of CHUNK windows: (a) every record of the chunk is copied into
+    // Chunks of CH windows: (a) every record of the chunk is copied into
     // shared memory by asynchronous copies (all in flight together, no
     // registers held); (b) each is advanced and, in modes P and F, written
     // back with its new cell while the slot request for it goes out; (c) once
     // all slot requests of the chunk are out, the records are written to
     // their rows.  One load latency and one slot latency per chunk.
-    for (int base = 0; base < N; base += 32 * CHUNK) {
+    for (int base = 0; base < N; base += 32 * CH) {
 #pragma unroll
-      for (int w = 0; w < CHUNK; ++w) {
+      for (int w = 0; w < CH; ++w) {
         const int m = base + (w << 5) + lane;
         if (m < N) {
           const R* p = member(m, owner_of(m));
@@ -894,10 +899,10 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       // (made by the first of them) and take consecutive slots, so their
       // records land side by side.  The atomic's result is read only when
       // the chunk is written.
-      uint32_t sbase[CHUNK];
-      int lr[CHUNK];  // leader lane | rank << 8
+      uint32_t sbase[CH];
+      int lr[CH];  // leader lane | rank << 8
 #pragma unroll
-      for (int w = 0; w < CHUNK; ++w) {
+      for (int w = 0; w < CH; ++w) {
         const int m = base + (w << 5) + lane;
         uint32_t key = 0xFFFFFFFFu;
         if (m < N) {
@@ -924,7 +929,7 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       }
       if (MODE != MODE_C) {
 #pragma unroll
-        for (int w = 0; w < CHUNK; ++w) {
+        for (int w = 0; w < CH; ++w) {
           const int m = base + (w << 5) + lane;
           const uint32_t slot = __shfl_sync(FULL, sbase[w], lr[w] & 255) + (uint32_t)(lr[w] >> 8);
           if (m < N) {
@@ -950,38 +955,62 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
   }
 }
 
-template <bool TH, int MODE, bool FO, bool BE, bool AT, bool ANG = false>
+template <bool TH, int MODE, bool FO, bool BE, bool AT, bool ANG = false, int CH = CHUNK>
 static void* warp_fn() {
-  return (void*)k_cells_warp<TH, MODE, FO, BE, AT, ANG>;
+  return (void*)k_cells_warp<TH, MODE, FO, BE, AT, ANG, CH>;
+}
+
+// pass-2 chunk depth of the F mode of the SRD variants (tuned); 3 elsewhere
+template <bool TH, bool FO, bool BE>
+static void* warp_fn_chunk(int ch) {
+  if (ch == 2) return warp_fn<TH, MODE_F, FO, BE, false, false, 2>();
+  if (ch == 4) return warp_fn<TH, MODE_F, FO, BE, false, false, 4>();
+  return warp_fn<TH, MODE_F, FO, BE, false, false, 3>();
 }
 
 template <int MODE, bool BE>
-static void* warp_variant_mb(bool thermo, bool force, bool at) {
+static void* warp_variant_mb(bool thermo, bool force, bool at, int ch) {
   if (at) return force ? warp_fn<false, MODE, true, BE, true>() : warp_fn<false, MODE, false, BE, true>();
+  if (MODE == MODE_F) {
+    if (thermo) return force ? warp_fn_chunk<true, true, BE>(ch) : warp_fn_chunk<true, false, BE>(ch);
+    return force ? warp_fn_chunk<false, true, BE>(ch) : warp_fn_chunk<false, false, BE>(ch);
+  }
   if (thermo) return force ? warp_fn<true, MODE, true, BE, false>() : warp_fn<true, MODE, false, BE, false>();
   return force ? warp_fn<false, MODE, true, BE, false>() : warp_fn<false, MODE, false, BE, false>();
 }
 
 template <int MODE>
-static void* warp_variant_mode(bool thermo, bool force, bool beads, bool at, bool ang) {
+static void* warp_variant_mode(bool thermo, bool force, bool beads, bool at, bool ang, int ch) {
   if (ang && thermo) return force ? warp_fn<true, MODE, true, false, false, true>()
                                   : warp_fn<true, MODE, false, false, false, true>();
   if (ang) return force ? warp_fn<false, MODE, true, false, false, true>()
                         : warp_fn<false, MODE, false, false, false, true>();
-  return beads ? warp_variant_mb<MODE, true>(thermo, force, at)
-               : warp_variant_mb<MODE, false>(thermo, force, at);
+  return beads ? warp_variant_mb<MODE, true>(thermo, force, at, ch)
+               : warp_variant_mb<MODE, false>(thermo, force, at, ch);
 }
 
 // ang: the angular-momentum correction (SRD without beads only).
-static void* warp_variant(bool thermo, bool force, bool beads, bool at, bool ang, int mode) {
-  if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force, beads, at, ang);
-  if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force, beads, at, ang);
-  return warp_variant_mode<MODE_C>(thermo, force, beads, at, ang);
+static void* warp_variant(bool thermo, bool force, bool beads, bool at, bool ang, int mode, int ch) {
+  if (mode == MODE_P) return warp_variant_mode<MODE_P>(thermo, force, beads, at, ang, ch);
+  if (mode == MODE_F) return warp_variant_mode<MODE_F>(thermo, force, beads, at, ang, ch);
+  return warp_variant_mode<MODE_C>(thermo, force, beads, at, ang, ch);
 }
 
-int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, bool ang, int mode) {
-  const void* fn = warp_variant(thermo, force, beads, at, ang, mode);
-  const size_t smem = block_smem(beads, at, ang);
+// the chunk depth a launch actually uses
+static int used_chunk(bool at, bool ang, int mode, int ch) {
+  return (mode == MODE_F && !at && !ang && (ch == 2 || ch == 4)) ? ch : CHUNK;
+}
+static size_t warp_smem(bool thermo, bool beads, bool at, bool ang, int ch) {
+  if (ch == 2) return block_smem<2>(beads, at, ang, thermo);
+  if (ch == 4) return block_smem<4>(beads, at, ang, thermo);
+  return block_smem<3>(beads, at, ang, thermo);
+}
+
+int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, bool ang, int mode,
+                             int chunk) {
+  const int ch = used_chunk(at, ang, mode, chunk);
+  const void* fn = warp_variant(thermo, force, beads, at, ang, mode, ch);
+  const size_t smem = warp_smem(thermo, beads, at, ang, ch);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, BLOCK, smem);
@@ -989,12 +1018,13 @@ int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, bool 
 }
 
 void launch_cells_warp(bool thermo, bool force, bool beads, bool at, bool ang, int mode,
-                       const BoxDev* boxes, const int2* spans, int nspans, int grid, int* err,
-                       cudaStream_t s) {
+                       const BoxDev* boxes, const int2* spans, int nspans, int grid, int chunk,
+                       int* err, cudaStream_t s) {
   if (nspans <= 0) return;
+  const int ch = used_chunk(at, ang, mode, chunk);
   void* args[] = {(void*)&boxes, (void*)&spans, (void*)&nspans, (void*)&err};
-  cudaLaunchKernel(warp_variant(thermo, force, beads, at, ang, mode), dim3(grid), dim3(BLOCK), args,
-                   block_smem(beads, at, ang), s);
+  cudaLaunchKernel(warp_variant(thermo, force, beads, at, ang, mode, ch), dim3(grid), dim3(BLOCK),
+                   args, warp_smem(thermo, beads, at, ang, ch), s);
 }
 
 }  // namespace mpcd

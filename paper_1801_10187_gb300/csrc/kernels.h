@@ -27,10 +27,14 @@ void launch_cells(bool mixed, int variant, int mode, const BoxDev* boxes, const 
 // instead of the rotation (thermo is then false).
 constexpr int WARP_MAX_K = 448;
 // ang (mixed model, SRD without beads): the angular-momentum correction.
-int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, bool ang, int mode);
+// chunk: windows of 32 members whose loads and slot requests pass 2 keeps in
+// flight together (2, 3 or 4; used by the F mode of the SRD variants, 3
+// elsewhere), a launch-tuner choice.
+int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, bool ang, int mode,
+                             int chunk);
 void launch_cells_warp(bool thermo, bool force, bool beads, bool at, bool ang, int mode,
-                       const BoxDev* boxes, const int2* spans, int nspans, int grid, int* err,
-                       cudaStream_t s);
+                       const BoxDev* boxes, const int2* spans, int nspans, int grid, int chunk,
+                       int* err, cudaStream_t s);
 // The FP64 model's counterpart (k_cells_warp_d.cu), same conditions.
 int cells_warpd_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode);
 void launch_cells_warpd(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,

@@ -85,10 +85,10 @@ struct BoxDev {
   double ca, sa, omc;   // cos(alpha), sin(alpha), 1 - cos(alpha)
   double g[3], hg[3], gdt[3], L[3];
   double md_h, md_hh;   // MD substep and half-kick factor (0.5 h) / M
-  // mixed model: E_k = hm es + 2^-33 ex from the exact energy sums (hm = m 2^-33)
-  double hm;
+  // mixed model: E_k Mt = hm2 (n S2 - |Q|^2) for a cell of solvent only (hm2 = m^2 2^-65)
+  double hm2;
   // parameters, float (mixed model)
-  float dt_f, kT_f, m_f, Mb_f, ca_f, sa_f, omc_f, hm_f;
+  float dt_f, kT_f, m_f, Mb_f, ca_f, sa_f, omc_f, pad_f;
   float g_f[3], hg_f[3], gdt_f[3], L_f[3];
   // particle storage (double buffered; cur selects the current set)
   void* rows[2];        // ncells * K records

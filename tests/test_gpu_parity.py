@@ -406,13 +406,15 @@ def test_mixed_row_capacity_limits(rho):
 
 
 def test_launch_tuner_keeps_results():
-    """mpcd_tune runs real steps under each candidate grid and keeps the
-    fastest; the trajectory is bit-identical to plain steps (mixed model)."""
+    """mpcd_tune runs real steps under every candidate (grid x pass-2 chunk
+    depth 2, 3, 4) and keeps the fastest; the trajectory is bit-identical to
+    plain steps (mixed model)."""
     s = inputs.solvent((24, 24, 24), 10, seed=51, mixed=True)
     a = pkg.Box(n=(24, 24, 24), seed=51, precision="mixed", thermostat=True)
     a.set_state(s.pos, s.vel)
-    bps, ms, taken = a.tune(1)
+    bps, ms, taken, chunk = a.tune(1)
     assert bps == -1 or bps >= 1
+    assert chunk in (2, 3, 4)
     assert ms > 0.0 and taken >= 2
     a.step(3)
     pa, va, *_, sta = a.get_state()
