@@ -222,19 +222,6 @@ __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, u
   n[2] = z;
 }
 
-__device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, uint32_t cell,
-                                        double n[3]) {
-  const uint4 w = draw(B, PURPOSE_ROT, cell, 0u, t);
-  const double a = (double)w.x * 0x1p-32;
-  const double b = (double)(4294967296LL - (long long)w.x) * 0x1p-32;
-  const double z = a - b;
-  const double r = 2.0 * sqrt(a * b);
-  const double phi = kTwoPi * ((double)w.y * 0x1p-32);
-  n[0] = r * cos(phi);
-  n[1] = r * sin(phi);
-  n[2] = z;
-}
-
 // Exact conversions to double on the integer pipe (the FP64 pipe of GB300
 // runs at about 1/64 of the FP32 rate and also executes the conversion
 // instructions): a float, and an integer 0 <= q < 2^53.  Other inputs (zero,
@@ -252,6 +239,23 @@ __device__ __forceinline__ double ll2d_exact(long long q) {
   const int lz = __clzll(q);  // the top bit of q at 63 - lz <= 52
   const unsigned long long m = (unsigned long long)q << (lz - 11);
   return __longlong_as_double((long long)(((unsigned long long)(1022 + 63 - lz) << 52) + m));
+}
+
+// FP64 model: u = w.x 2^-32, z = 2u - 1, sqrt(1 - z^2) = 2 sqrt(u (1 - u)) and
+// phi = 2 pi w.y 2^-32, with the words converted on the integer pipe and
+// (sin phi, cos phi) from one sincospi of phi / pi = w.y 2^-31 (exact).
+__device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, uint32_t cell,
+                                        double n[3]) {
+  const uint4 w = draw(B, PURPOSE_ROT, cell, 0u, t);
+  const double a = ll2d_exact((long long)w.x) * 0x1p-32;
+  const double b = ll2d_exact(4294967296LL - (long long)w.x) * 0x1p-32;
+  const double z = a - b;
+  const double r = 2.0 * sqrt(a * b);
+  double sp, cp;
+  sincospi(ll2d_exact((long long)w.y) * 0x1p-31, &sp, &cp);
+  n[0] = r * cp;
+  n[1] = r * sp;
+  n[2] = z;
 }
 
 // Mixed model, Eq. (thermo): xi = sqrt(E^/E_k) to double accuracy, rounded to
@@ -383,7 +387,7 @@ __device__ inline bool gamma_draw(const BoxDev& B, unsigned long long t, uint32_
     const uint4 wa = draw(B, PURPOSE_THERMO, cell, 1u + 2u * j, t);
     const uint4 wb = draw(B, PURPOSE_THERMO, cell, 2u + 2u * j, t);
     const double U1 = unit53(wa.x, wb.x), U2 = unit53(wa.z, wb.z), U3 = unit53(wa.y, wb.y);
-    const double x = sqrt(-2.0 * log(1.0 - U1)) * cos(kTwoPi * U2);
+    const double x = sqrt(-2.0 * log(1.0 - U1)) * cospi(2.0 * U2);  // cos(2 pi U2)
     const double t1 = 1.0 + c * x;
     if (!(t1 > 0.0)) continue;
     const double v = t1 * t1 * t1;
@@ -429,10 +433,10 @@ __device__ __forceinline__ void at_draw(const BoxDev& B, unsigned long long t, u
   const double U3 = unit53(wa.z, wb.z), U4 = unit53(wa.w, wb.w);
   const double r1 = sqrt(-2.0 * log(1.0 - U1)), r2 = sqrt(-2.0 * log(1.0 - U3));
   double s1, c1;
-  sincos(kTwoPi * U2, &s1, &c1);  // one argument reduction for the pair
+  sincospi(2.0 * U2, &s1, &c1);  // angle 2 pi U2 (2 U2 exact): no argument reduction
   dv[0] = sigma * (r1 * c1);
   dv[1] = sigma * (r1 * s1);
-  dv[2] = sigma * (r2 * cos(kTwoPi * U4));
+  dv[2] = sigma * (r2 * cospi(2.0 * U4));
 }
 
 // ---------------------------------------------------------------------------
@@ -466,7 +470,7 @@ __device__ __forceinline__ void virtual_velocity(const BoxDev& B, unsigned long 
   for (int k = 0; k < 3; ++k) {
     const uint4 w = draw(B, PURPOSE_VIRT, cell, 1u + 3u * (uint32_t)q + (uint32_t)k, t);
     const double U = unit53(w.x, w.y), U2 = unit53(w.z, w.w);
-    vv[k] = B.sigma_virt * (sqrt(-2.0 * log(1.0 - U)) * cos(kTwoPi * U2));
+    vv[k] = B.sigma_virt * (sqrt(-2.0 * log(1.0 - U)) * cospi(2.0 * U2));
   }
 }
 

@@ -28,6 +28,38 @@ __device__ __forceinline__ double wrap(double x, double L) {
   return x;
 }
 
+// The same wrap with its common case settled on the bit pattern: for L > 0 a
+// double with +0 <= x < L is exactly one whose bits, read as an unsigned
+// integer, are below L's (negatives and -0 carry the sign bit, NaN and x >= L
+// sit above), and wrap() returns such an x unchanged.  Everything else takes
+// wrap() itself, so the result is wrap()'s for every x; only the compare
+// leaves the FP64 pipe.
+__device__ __forceinline__ double wrap_bits(double x, double L) {
+  if ((unsigned long long)__double_as_longlong(x) < (unsigned long long)__double_as_longlong(L))
+    return x;
+  return wrap(x, L);
+}
+
+// floor(RN(x - s)), the double expression of Sec. 3.4's cell index, for x = +-0
+// or 0 <= x < 2^21 and s = S 2^-32 in [-1/2, 1/2), in integer arithmetic.  S
+// is an integer, so floor(x - s) = floor((floor(x 2^32) - S) 2^-32), and
+// floor(x 2^32) is x's significand shifted by its exponent.  The rounded
+// difference has the same floor except at one point: a difference that
+// rounds must leave x's binade upwards (s < 0), so for x >= 1/2 it lies in
+// [2^j, 2^j + 1/2] above the integer 2^j, and for x < 1/2 it is at most
+// 1 - 2^-54, which rounds (to even) up to 1 only for x = 1/2 - 2^-54 and
+// s = -1/2.  Above 2^21 (boxes with more cells per axis) the double
+// expression itself is used.
+__device__ __forceinline__ int floor_minus_shift(double x, long long S, double s) {
+  const long long b = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL;
+  const int e = (int)(b >> 52);  // biased exponent; x 2^32 = m 2^(e - 1043)
+  if (e >= 1044) return (int)floor(x - s);
+  if (b == 0x3FDFFFFFFFFFFFFFLL && S == -2147483648LL) return 1;
+  const long long m = (b & 0x000FFFFFFFFFFFFFLL) | 0x0010000000000000LL;
+  const long long X = m >> min(1043 - e, 63);  // 0 for zeros and subnormals
+  return (int)((X - S) >> 32);
+}
+
 // ---------------------------------------------------------------------------
 // Eq. (stream): r <- r + v dt (+ g dt^2 / 2, v <- v + g dt).  With walls in z
 // the particle reaches the wall at tau, its velocity is reversed (no-slip

@@ -13,7 +13,8 @@
 //            component when the cell changes
 //   cell     lane c forms u of cell c, draws the axis (and with the
 //            thermostat, after the same kind of pass for the energy about u,
-//            xi) and leaves them in shared memory
+//            xi) and leaves the collision in shared memory as the affine
+//            map v' = A v + c (A = xi R, c = u - A u)
 //   pass 2   windows of 32 members: records copied to shared memory by
 //            cp.async, collided, streamed, binned under the next shift; lanes
 //            bound for the same cell share one slot atomic
@@ -48,7 +49,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 struct WarpShared {
-  double2 pr[4][32];               // (u0, u1), (u2, xi), (axis0, axis1), (axis2, 0) per cell
+  double2 pr[6][32];               // per cell: rows (A_i0, A_i1), (A_i2, c_i) of the collision
+                                   // map; before that (u0, u1), (u2, xi), (axis0, axis1), (axis2, 0)
   double P[3][32];                 // sum of v over the cell's solvent
   double E[32];                    // sum of |v - u|^2 over the cell's solvent
   int offs[33];                    // first member of each cell; offs[32] = members
@@ -301,12 +303,13 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
 #pragma unroll
               for (int q = 0; q < 3; ++q) Pv[q] += w[q];
             }
-        M = (double)n * H.m + (double)nb * H.Mb;
+        M = ll2d_exact((long long)n) * H.m + ll2d_exact((long long)nb) * H.Mb;
+        const double iM = 1.0 / M;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           double P = H.m * Pv[q];
           if (BEADS && gnb > 0) P += BS.X[q][lane];
-          u[q] = P / M;
+          u[q] = P * iM;
         }
         W.pr[0][lane] = make_double2(u[0], u[1]);
         W.pr[1][lane] = make_double2(u[2], 1.0);
@@ -409,13 +412,47 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
           }
         }
       }
+      // pass 2 takes the collision of Eq. srd as one affine map per cell,
+      // v' = A v + c with A = xi R(axis, alpha) and c = u - A u (Rodrigues'
+      // R = cos(alpha) I + sin(alpha) [n]x + (1 - cos(alpha)) n n^T): nine
+      // FP64 fmas a member instead of the subtract, rotate and add.
+      auto put_map = [&](const double uu[3], double x, const double nn[3]) {
+        const double ca = H.ca, sa = H.sa, omc = H.omc;
+        double A[3][3];
+        A[0][0] = fma(omc * nn[0], nn[0], ca);
+        A[1][1] = fma(omc * nn[1], nn[1], ca);
+        A[2][2] = fma(omc * nn[2], nn[2], ca);
+        A[0][1] = fma(omc * nn[0], nn[1], -sa * nn[2]);
+        A[1][0] = fma(omc * nn[1], nn[0], sa * nn[2]);
+        A[0][2] = fma(omc * nn[0], nn[2], sa * nn[1]);
+        A[2][0] = fma(omc * nn[2], nn[0], -sa * nn[1]);
+        A[1][2] = fma(omc * nn[1], nn[2], -sa * nn[0]);
+        A[2][1] = fma(omc * nn[2], nn[1], sa * nn[0]);
+        double c[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            if (THERMO) A[i][k] *= x;
+          c[i] = uu[i] - fma(A[i][0], uu[0], fma(A[i][1], uu[1], A[i][2] * uu[2]));
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          W.pr[2 * i][lane] = make_double2(A[i][0], A[i][1]);
+          W.pr[2 * i + 1][lane] = make_double2(A[i][2], c[i]);
+        }
+      };
       if (occupied && !AT) {
         double ax[3];
         axis_of(B, t, (uint32_t)cell, ax);  // Sec. 3.6
-        W.pr[0][lane] = make_double2(u[0], u[1]);
-        W.pr[1][lane] = make_double2(u[2], xi);
-        W.pr[2][lane] = make_double2(ax[0], ax[1]);
-        W.pr[3][lane] = make_double2(ax[2], 0.0);
+        if (BEADS) {  // the beads collide with u, xi and the axis first
+          W.pr[0][lane] = make_double2(u[0], u[1]);
+          W.pr[1][lane] = make_double2(u[2], xi);
+          W.pr[2][lane] = make_double2(ax[0], ax[1]);
+          W.pr[3][lane] = make_double2(ax[2], 0.0);
+        } else {
+          put_map(u, xi, ax);
+        }
       }
       __syncwarp();
       if (BEADS && !AT && gnb > 0) {  // collide the beads with their cell's parameters
@@ -432,6 +469,15 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
           B.svel[3 * b + 2] = w[2];
         });
       }
+      if (BEADS && !AT) {
+        __syncwarp();
+        if (occupied) {
+          const double2 p0 = W.pr[0][lane], p1 = W.pr[1][lane], p2 = W.pr[2][lane],
+                        p3 = W.pr[3][lane];
+          const double uu[3] = {p0.x, p0.y, p1.x}, nn[3] = {p2.x, p2.y, p3.x};
+          put_map(uu, p1.y, nn);
+        }
+      }
       __syncwarp();
     }
 
@@ -444,16 +490,15 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
         w[0] = (p0.x + dv[0]) - p2.x;
         w[1] = (p0.y + dv[1]) - p2.y;
         w[2] = (p1.x + dv[2]) - p3.x;
-      } else if (MODE != MODE_P) {
-        const double2 p0 = W.pr[0][o], p1 = W.pr[1][o], p2 = W.pr[2][o], p3 = W.pr[3][o];
-        const double nn[3] = {p2.x, p2.y, p3.x};
-        const double uu[3] = {p0.x, p0.y, p1.x};
-        double d[3], rr[3];
+      } else if (MODE != MODE_P) {  // Eq. srd as v' = A v + c
+        double v2[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) d[q] = w[q] - uu[q];
-        rotate(nn, H.ca, H.sa, H.omc, d, rr);
+        for (int i = 0; i < 3; ++i) {
+          const double2 a = W.pr[2 * i][o], b = W.pr[2 * i + 1][o];
+          v2[i] = fma(a.x, w[0], fma(a.y, w[1], fma(b.x, w[2], b.y)));
+        }
 #pragma unroll
-        for (int q = 0; q < 3; ++q) w[q] = uu[q] + (THERMO ? p1.y * rr[q] : rr[q]);
+        for (int i = 0; i < 3; ++i) w[i] = v2[i];
       }
       if (MODE == MODE_C) return 0u;
       int c[3];
@@ -466,8 +511,8 @@ __global__ void __launch_bounds__(BLOCK, 3) k_cells_warp_d(const BoxDev* __restr
         } else {
           r[q] = fma(w[q], H.dt, r[q]);  // FP64 parity is to rounding: no -0 -> +0 step
         }
-        r[q] = wrap(r[q], H.L[q]);  // finite, in [0, L)
-        int i = (int)floor(r[q] - H.s[q]);  // in [-1, n]: floor(x - s) exactly (Sec. 3.4)
+        r[q] = wrap_bits(r[q], H.L[q]);  // finite, in [0, L) (or -0)
+        int i = floor_minus_shift(r[q], H.S[q], H.s[q]);  // in [-1, n] (Sec. 3.4)
         if (i < 0) i += H.n[q];
         if (i >= H.n[q]) i -= H.n[q];
         if (i < 0 || i >= H.n[q]) {

@@ -167,9 +167,14 @@ __device__ __forceinline__ uint4 draw(const BoxDev& B, uint32_t purpose, uint32_
 }
 
 // [0,1) from the top 53 bits of the 64-bit word (hi, lo).
+// k 2^-53 for the top 53 bits k of (hi, lo), built from k's bits on the
+// integer pipe (exact, so the same double as converting k and scaling).
 __device__ __forceinline__ double unit53(uint32_t hi, uint32_t lo) {
-  const unsigned long long x = ((unsigned long long)hi << 32) | lo;
-  return (double)(x >> 11) * 0x1p-53;
+  const unsigned long long k = (((unsigned long long)hi << 32) | lo) >> 11;
+  if (k == 0ull) return 0.0;
+  const int lz = __clzll((long long)k);  // 11..63: k's top bit at 63 - lz
+  const unsigned long long m = k << (lz - 11);  // top bit at 52: adds one to the exponent
+  return __longlong_as_double((long long)(((unsigned long long)(1032 - lz) << 52) + m));
 }
 
 // Grid shift of step t, in units of 2^-32 cell edges: S in [-2^31, 2^31).
