@@ -154,25 +154,6 @@ __device__ __forceinline__ float series_log(float x) {
   return (e >= 0 ? small_to_float(e) : -small_to_float(-e)) * ln2 + (2.0f * t) * series;
 }
 
-// series_log for a normal positive float x <= 1: the same operations without
-// the special cases.
-__device__ __forceinline__ float series_log_unit(float x) {
-  uint32_t b = __float_as_uint(x);
-  int e = (int)((b >> 23) & 0xFFu) - 127;
-  float m = __uint_as_float((b & 0x7FFFFFu) | 0x3F800000u);
-  if (m > 1.41421354f) {
-    m = m * 0.5f;
-    e += 1;
-  }
-  const float t = (m - 1.0f) / (m + 1.0f);
-  const float t2 = t * t;
-  const float l3 = (float)(1.0 / 3.0), l5 = (float)(1.0 / 5.0), l7 = (float)(1.0 / 7.0);
-  const float l9 = (float)(1.0 / 9.0), l11 = (float)(1.0 / 11.0);
-  const float series = 1.0f + t2 * (l3 + t2 * (l5 + t2 * (l7 + t2 * (l9 + t2 * l11))));
-  const float ln2 = (float)0.69314718055994530942;
-  return (e >= 0 ? small_to_float(e) : -small_to_float(-e)) * ln2 + (2.0f * t) * series;
-}
-
 // rne(q) as a float for 0 <= q < 2^63, on the integer pipe.
 __device__ __forceinline__ float u63_to_float(unsigned long long q) { return i64_to_float((long long)q); }
 
@@ -182,30 +163,51 @@ __device__ __forceinline__ float u63_to_float(unsigned long long q) { return i64
 // (series through t^15, t <= 1/3), free of the cancellation of 1 - U near 1;
 // otherwise -ln(e), e = 1 - U = (2^32 - hi) 2^-32, or, in the far tail, e
 // from all 53 bits, (2^32 - hi) 2^21 - lo / 2^11 in units of 2^-53, so that
-// the radius follows the FP64 model's uniform there.
+// the radius follows the FP64 model's uniform there; ln(e) by the operations
+// of series_log (e is a normal float <= 1).  Both ranges share one division
+// and one Horner chain: the second range takes its two highest coefficients
+// as zero, which leaves every rounding of its shorter series unchanged, and
+// its exponent term is zero in the first range (adding +0 changes nothing),
+// so a warp whose lanes fall in both ranges runs the series once.
 template <class LoOf>
 __device__ __forceinline__ float neg_log1m(uint32_t hi, LoOf lo_of) {
-  if (hi < 0x80000000u) {
+  const bool low = hi < 0x80000000u;
+  float num, den;
+  int ex = 0;
+  if (low) {
     const float U = word_to_float(hi) * 0x1p-32f;
-    const float t = U / (2.0f - U);
-    const float t2 = t * t;
-    const float l3 = (float)(1.0 / 3.0), l5 = (float)(1.0 / 5.0), l7 = (float)(1.0 / 7.0);
-    const float l9 = (float)(1.0 / 9.0), l11 = (float)(1.0 / 11.0), l13 = (float)(1.0 / 13.0);
-    const float l15 = (float)(1.0 / 15.0);
-    const float series =
-        1.0f + t2 * (l3 + t2 * (l5 + t2 * (l7 + t2 * (l9 + t2 * (l11 + t2 * (l13 + t2 * l15))))));
-    return (2.0f * t) * series;
-  }
-  float e;
-  if (hi < 0xFFF00000u) {
-    e = comp_word_to_float(hi) * 0x1p-32f;
+    num = U;
+    den = 2.0f - U;
   } else {
-    const uint32_t lo = lo_of();
-    const unsigned long long q =
-        ((unsigned long long)(0u - hi) << 21) - (unsigned long long)(lo >> 11);
-    e = u63_to_float(q) * 0x1p-53f;
+    float e;
+    if (hi < 0xFFF00000u) {
+      e = comp_word_to_float(hi) * 0x1p-32f;
+    } else {
+      const uint32_t lo = lo_of();
+      const unsigned long long q =
+          ((unsigned long long)(0u - hi) << 21) - (unsigned long long)(lo >> 11);
+      e = u63_to_float(q) * 0x1p-53f;
+    }
+    const uint32_t b = __float_as_uint(e);
+    ex = (int)((b >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((b & 0x7FFFFFu) | 0x3F800000u);
+    if (m > 1.41421354f) {
+      m = m * 0.5f;
+      ex += 1;
+    }
+    num = m - 1.0f;
+    den = m + 1.0f;
   }
-  return -series_log_unit(e);
+  const float t = num / den;
+  const float t2 = t * t;
+  const float l3 = (float)(1.0 / 3.0), l5 = (float)(1.0 / 5.0), l7 = (float)(1.0 / 7.0);
+  const float l9 = (float)(1.0 / 9.0), l11 = (float)(1.0 / 11.0);
+  const float l13 = low ? (float)(1.0 / 13.0) : 0.0f, l15 = low ? (float)(1.0 / 15.0) : 0.0f;
+  const float series =
+      1.0f + t2 * (l3 + t2 * (l5 + t2 * (l7 + t2 * (l9 + t2 * (l11 + t2 * (l13 + t2 * l15))))));
+  const float ln2 = (float)0.69314718055994530942;
+  const float r = (ex >= 0 ? small_to_float(ex) : -small_to_float(-ex)) * ln2 + (2.0f * t) * series;
+  return low ? r : -r;
 }
 
 __device__ __forceinline__ void axis_of(const BoxDev& B, unsigned long long t, uint32_t cell,

@@ -181,6 +181,50 @@ def test_clustered_input_takes_cooperative_path(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("steps", [1, 3])
+def test_rows_overflowing_by_a_few(precision, steps):
+    """Tight clusters push some cells a few members past the row capacity (36
+    at density 10), three of them in one warp's span: their extra members go
+    to the overflow list and come back through it.  Results match the
+    oracle."""
+    rng = np.random.default_rng(11)
+    n = (16, 16, 16)
+    s = inputs.solvent(n, 10, seed=12, mixed=precision == "mixed")
+    cells = [tuple(c) for c in rng.integers(0, 16, size=(40, 3))]
+    cells += [(4, 9, 9), (5, 9, 9), (6, 9, 9)]  # one warp's span, 3 x 40 extra members
+    extra_p, extra_v = [], []
+    for k, c in enumerate(cells):
+        m = 40 if k >= 40 else int(rng.integers(20, 41))
+        extra_p.append(np.array(c, float) + 0.45 + 0.1 * rng.random((m, 3)))
+        extra_v.append(rng.standard_normal((m, 3)))
+    pos = np.vstack([s.pos] + extra_p)
+    vel = np.vstack([s.vel] + extra_v)
+    if precision == "mixed":
+        pos = pos.astype(np.float32).astype(np.float64)
+        vel = vel.astype(np.float32).astype(np.float64)
+    box = pkg.Box(n=n, seed=12, precision=precision, thermostat=True)
+    box.set_state(pos, vel)
+    box.step(steps)
+    p2, v2, *_ = box.get_state()
+    got_cells, counts = box.last_cells()
+    box.close()
+    ref = oracle.State(pos.copy(), vel.copy())
+    rc, rk = oracle.step(oracle.Params(n=n, seed=12, thermostat=True,
+                                       precision=oracle.MIXED if precision == "mixed" else oracle.FP64),
+                         ref, steps, want_cells=True)
+    if steps == 1:
+        assert counts.max() > 36  # beyond the row capacity
+    assert np.array_equal(got_cells, rc)
+    assert np.array_equal(counts, rk)
+    if precision == "mixed":
+        assert np.array_equal(p2, ref.pos) and np.array_equal(v2, ref.vel)
+    else:
+        d = np.abs(p2 - ref.pos)
+        assert np.minimum(d, 16.0 - d).max() <= 1e-12
+        assert rel_err(v2, ref.vel) <= 1e-12 * steps
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_edge_cases_empty_single_and_one_cell_box(precision):
     # empty state
     box = pkg.Box(n=(3, 3, 3), precision=precision)
