@@ -26,6 +26,11 @@ __device__ __forceinline__ void cp_async16_last_use(void* smem, const void* gmem
                "l"(pol)
                : "memory");
 }
+// 16-byte global -> shared asynchronous copy (L2 only, default eviction).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void store_rec_streaming(RecF* p, const float r[3], const float v[3],
                                                     uint32_t tag, unsigned long long pol) {
   asm volatile("st.global.L2::cache_hint.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8}, %9;" ::"l"(p),

@@ -54,6 +54,7 @@ constexpr int WARPS = BLOCK / 32;
 
 constexpr int MAP_MEMBERS = 640;  // members per warp with a byte owner map
 constexpr int STAGE = 256;        // member velocities staged per block of pass 1
+constexpr int STAGE4 = 192;       // the same for the SRD variants (whole 16-byte words)
 constexpr int STAGE_PAD = STAGE + STAGE / 32;
 constexpr int CHUNK = 3;          // windows of 32 members per chunk of pass 2 (default)
 
@@ -76,6 +77,7 @@ struct WarpShared {
   unsigned char map[MAP_MEMBERS];  // owner lane of each member
   union {
     float sv[3][STAGE_PAD];        // pass 1: staged velocities (index j + j / 32)
+    float4 sv4[STAGE4];            // pass 1 of the SRD variants: staged (v, tag)
     float4 buf[CH][2][32];         // pass 2: records of one chunk (two halves)
   };
 };
@@ -189,6 +191,10 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
   AngWarp& AG = reinterpret_cast<AngWarp*>(smem_ + block_smem<CH>(BEADS, AT) + sizeof(AngBlock))[threadIdx.x >> 5];
   ThermoShared& TS = reinterpret_cast<ThermoShared*>(smem_ + block_smem<CH>(BEADS, AT, ANG))[threadIdx.x >> 5];
   const SpanParams& H = sp_;
+  // SRD variants stage pass 1 by asynchronous copies issued early (above);
+  // the Andersen and angular variants load and convert in stage()
+  constexpr bool EARLY = !AT && !ANG;
+  constexpr int SB = EARLY ? STAGE4 : STAGE;
   int box_of_params = -1;  // the span parameters depend on the box only
   for (int sp = blockIdx.x; sp < nspans; sp += gridDim.x) {
     const int2 tt = spans[sp];
@@ -331,9 +337,9 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       }
       __syncwarp();
     };
-    // This lane's consecutive share of a staged block: f(o, js, last) with the
-    // owner lane o, the (padded) index js in the block and whether it is the
-    // last of the share in cell o.
+    // This lane's consecutive share of a staged block: f(o, j, last) with the
+    // owner lane o, the index j in the block and whether it is the last of
+    // the share in cell o.
     auto share = [&](int sbase, int cnt, auto&& f) {
       const int cs = (lane * cnt) >> 5, ce = ((lane + 1) * cnt) >> 5;
       if (cs >= ce) return;
@@ -346,9 +352,20 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
             cend = W.offs[o + 1] - sbase;
           } while (cend == j);
         }
-        f(o, j + (j >> 5), j + 1 == cend || j + 1 == ce);
+        f(o, j, j + 1 == cend || j + 1 == ce);
       }
     };
+
+    // SRD variants: the (v, tag) words of members [sbase, sbase + cnt) are
+    // copied into shared memory asynchronously.  The first block is issued
+    // here, before the bead sums and the per-cell draws, which need none of
+    // it, so its load latency passes while they compute.
+    auto stage_async = [&](int sbase, int cnt) {
+      for (int j = lane; j < cnt; j += 32)
+        cp_async16(&W.sv4[j], member(sbase + j, owner_of(sbase + j)));
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (EARLY && MODE != MODE_P) stage_async(0, min(STAGE4, N));
 
     // Solute beads join their cell's collision with mass M (Sec. 3.6).  The
     // 32 cells of the warp are one bead group; its beads are handled one per
@@ -420,14 +437,32 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       }
       __syncwarp();
       bool slow = false, slow_d = false;
-      for (int sbase = 0; sbase < N; sbase += STAGE) {
-        const int cnt = min(STAGE, N - sbase);
-        stage(sbase, cnt);
+      for (int sbase = 0; sbase < N; sbase += SB) {
+        const int cnt = min(SB, N - sbase);
+        if (EARLY) {
+          if (sbase > 0) stage_async(sbase, cnt);
+          cp_async_wait_all();
+          __syncwarp();  // every lane's copies are in shared memory
+        } else {
+          stage(sbase, cnt);
+        }
         int Hs[3] = {0, 0, 0}, Ls[3] = {0, 0, 0};
         int Hd[3] = {0, 0, 0}, Ld[3] = {0, 0, 0};
         int Hq[3] = {0, 0, 0}, Lq[3] = {0, 0, 0};
         long long Shh = 0, Shl = 0, Sll = 0;  // thermostat: second moment
-        share(sbase, cnt, [&](int o, int js, bool last) {
+        share(sbase, cnt, [&](int o, int j, bool last) {
+          const int js = j + (j >> 5);
+          float vm[3];
+          if (EARLY) {
+            const float4 a = W.sv4[j];
+            vm[0] = a.x;
+            vm[1] = a.y;
+            vm[2] = a.z;
+          } else {
+            vm[0] = W.sv[0][js];
+            vm[1] = W.sv[1][js];
+            vm[2] = W.sv[2][js];
+          }
           if (ANG) {  // |position in the cell frame| < 2: the split never fails
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -440,7 +475,7 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             int h, l;
-            if (!split32(W.sv[q][js], h, l)) {
+            if (!split32(vm[q], h, l)) {
               slow = true;
               h = 0;
               l = 0;
@@ -455,8 +490,8 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
           }
           if (AT) {  // Eq. at: this member's random velocity, summed the same way
             float dv[3];
-            const int mp = sbase + (sbase >> 5) + js;  // padded member index
-            if (sbase + js - js / 33 < DVC) {  // js = j + j / 32, so j = js - js / 33
+            const int m = sbase + j, mp = m + (m >> 5);  // member, padded index
+            if (m < DVC) {
               dv[0] = AS.dv[0][mp];
               dv[1] = AS.dv[1][mp];
               dv[2] = AS.dv[2][mp];
@@ -717,7 +752,8 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
           const int cnt = min(STAGE, N - sbase);
           if (N > STAGE) stage(sbase, cnt);  // else still staged from pass 1
           int Ha[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, La[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-          share(sbase, cnt, [&](int o, int js, bool last) {
+          share(sbase, cnt, [&](int o, int j, bool last) {
+            const int js = j + (j >> 5);
             const float v[3] = {W.sv[0][js], W.sv[1][js], W.sv[2][js]};
             const float x[3] = {AG.sr[0][js], AG.sr[1][js], AG.sr[2][js]};
             float tm[9];
