@@ -326,9 +326,9 @@ def main():
     box.step(W)
     # launch tuner on real warm-up steps (grid of the fused pass), then the
     # re-captured step graph warms up again
-    tuned_bps, tuned_ms, _, tuned_chunk = box.tune(2)
-    config["launch"] = {"blocks_per_sm": tuned_bps if tuned_bps > 0 else "one per span",
-                        "pass2_chunk": tuned_chunk, "cells_per_warp": 32,
+    tuned_bps, tuned_ms, _, tuned_chunk, tuned_cpw = box.tune(2)
+    config["launch"] = {"blocks_per_sm": tuned_bps if tuned_bps > 0 else "one per span part",
+                        "pass2_chunk": tuned_chunk, "cells_per_warp": tuned_cpw,
                         "tuner_ms_per_step": tuned_ms}
     box.step(2)
     torch.cuda.synchronize()

@@ -168,21 +168,25 @@ int mpcd_set_state_thermal(mpcd_ctx* ctx, int64_t n_solvent, uint64_t init_seed,
  * Errors: ESTATE, EINVAL (nsteps < 0), ECUDA. */
 int mpcd_step(mpcd_ctx* ctx, int64_t nsteps);
 
-/* Launch tuner (the paper tunes its kernels' launch parameters on real steps
- * at run time, Sec. 3.5 and Sec. 4): each candidate of the fused step kernel
- * -- its grid (1 up to the occupancy limit of blocks per SM, and one block per
- * 256-cell span) times, for mixed boxes with the SRD rule and no angular
- * correction, the depth of pass 2 (2, 3 or 4 windows of 32 members whose
- * record loads and slot requests are in flight together) -- runs
- * steps_per_candidate real steps, timed with CUDA events; the fastest is kept
- * for later steps.  The simulation advances by *steps_taken steps (one more
- * when the first step must stream and bin).  Results do not depend on the
- * candidate (mixed model bit for bit; FP64 to rounding).  Outputs may be
- * NULL: *blocks_per_sm (-1 = one block per span), *ms_per_step of the winner,
- * *pass2_chunk (windows per chunk).  Synchronises.  Errors: EINVAL, ESTATE,
- * ECUDA, EDEVICE. */
+/* Launch tuner (the paper tunes its kernels' launch parameters, among them
+ * the threads per cell, on real steps at run time, Sec. 3.5 and Sec. 4): each
+ * candidate of the fused step kernel -- its grid (1 up to the occupancy limit
+ * of blocks per SM, and one block per span part) times, for mixed boxes with
+ * the SRD rule and no angular correction, the cells each warp owns and the
+ * depth of pass 2: 32 cells per warp with 2, 3 or 4 windows of 32 members
+ * whose record loads and slot requests are in flight together, and 16 or 8
+ * cells per warp with 3 (a 256-cell span is then taken in 2 or 4 parts, one
+ * block each: more blocks for a small box, idle lanes in the per-cell work)
+ * -- runs steps_per_candidate real steps, timed with CUDA events; the fastest
+ * is kept for later steps.  The simulation advances by *steps_taken steps (one
+ * more when the first step must stream and bin).  Results do not depend on
+ * the candidate (mixed model bit for bit; FP64 to rounding).  Outputs may be
+ * NULL: *blocks_per_sm (-1 = one block per span part), *ms_per_step of the
+ * winner, *pass2_chunk (windows per chunk), *cells_per_warp (32, 16 or 8).
+ * Synchronises.  Errors: EINVAL, ESTATE, ECUDA, EDEVICE. */
 int mpcd_tune(mpcd_ctx* ctx, int64_t steps_per_candidate, int32_t* blocks_per_sm,
-              double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk);
+              double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk,
+              int32_t* cells_per_warp);
 
 /* Copy the state out in input (tag) order; arrays as for set_state (solute
  * arrays may be NULL).  Synchronises.  Errors: ESTATE, ECUDA, EDEVICE. */
@@ -277,7 +281,8 @@ int mpcd_batch_step(mpcd_batch* b, int64_t nsteps);
 
 /* mpcd_tune for every resident box together (one choice for the batch). */
 int mpcd_batch_tune(mpcd_batch* b, int64_t steps_per_candidate, int32_t* blocks_per_sm,
-                    double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk);
+                    double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk,
+                    int32_t* cells_per_warp);
 
 /* Copy one box's state out (tag order).  Synchronises. */
 int mpcd_batch_get_state(mpcd_batch* b, int32_t slot, double* pos, double* vel,

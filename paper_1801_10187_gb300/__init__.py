@@ -112,8 +112,8 @@ def lib():
     L.mpcd_box_footprint.restype = i64
     L.mpcd_batch_add.argtypes = [vp, P(_Params), i64, dp, dp, u64, P(i32)]
     L.mpcd_batch_step.argtypes = [vp, i64]
-    L.mpcd_tune.argtypes = [vp, i64, P(i32), dp, P(i64), P(i32)]
-    L.mpcd_batch_tune.argtypes = [vp, i64, P(i32), dp, P(i64), P(i32)]
+    L.mpcd_tune.argtypes = [vp, i64, P(i32), dp, P(i64), P(i32), P(i32)]
+    L.mpcd_batch_tune.argtypes = [vp, i64, P(i32), dp, P(i64), P(i32), P(i32)]
     L.mpcd_batch_get_state.argtypes = [vp, i32, dp, dp, P(u64)]
     L.mpcd_batch_observables.argtypes = [vp, i32, P(_Obs)]
     L.mpcd_batch_remove.argtypes = [vp, i32]
@@ -179,10 +179,10 @@ def make_params(n=(10, 10, 10), dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=
 
 def _tune(fn, handle, steps_per_candidate):
     bps, ms, taken = ctypes.c_int32(0), ctypes.c_double(0.0), ctypes.c_int64(0)
-    chunk = ctypes.c_int32(0)
+    chunk, cpw = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(fn(handle, int(steps_per_candidate), ctypes.byref(bps), ctypes.byref(ms),
-              ctypes.byref(taken), ctypes.byref(chunk)))
-    return bps.value, ms.value, taken.value, chunk.value
+              ctypes.byref(taken), ctypes.byref(chunk), ctypes.byref(cpw)))
+    return bps.value, ms.value, taken.value, chunk.value, cpw.value
 
 
 def _obs_dict(o: _Obs) -> dict:
@@ -245,7 +245,7 @@ class Box:
     def tune(self, steps_per_candidate=2):
         """Launch tuner (mpcd_tune): returns (blocks per SM or -1, ms per
         step of the choice, steps the simulation advanced, pass-2 chunk
-        depth)."""
+        depth, cells per warp)."""
         return _tune(lib().mpcd_tune, self._ctx, steps_per_candidate)
 
     def get_state(self):
@@ -351,7 +351,7 @@ class Batch:
 
     def tune(self, steps_per_candidate=2):
         """mpcd_batch_tune: (blocks per SM or -1, ms per step, steps taken,
-        pass-2 chunk depth)."""
+        pass-2 chunk depth, cells per warp)."""
         return _tune(lib().mpcd_batch_tune, self._b, steps_per_candidate)
 
     def get_state(self, slot: int):

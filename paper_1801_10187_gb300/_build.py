@@ -16,8 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpcd.so")
-SOURCES = ["k_step.cu", "k_cells.cu", "k_cells_warp.cu", "k_cells_warp_d.cu", "k_obs.cu", "k_wca.cu",
-           "capi.cu"]
+SOURCES = ["k_step.cu", "k_cells.cu", "k_cells_warp.cu", "k_cells_warp_narrow.cu",
+           "k_cells_warp_d.cu", "k_obs.cu", "k_wca.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]

@@ -22,6 +22,7 @@
 #include <string>
 #include <thread>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/mpcd.h"
@@ -307,6 +308,10 @@ struct Engine {
   // depth (2, 3, 4), and the depth in use (a launch-tuner choice)
   int bps_chunk[5][NVAR] = {};
   int tuned_chunk = 3;
+  // the same variants with 16 and 8 cells per warp (chunks of 3), and the
+  // cells per warp in use (a launch-tuner choice)
+  int bps_narrow[2][NVAR] = {};
+  int tuned_cpw = 32;
 
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // MODE_P, MODE_F, MODE_C
   bool tables_ok = false;
@@ -330,11 +335,11 @@ struct Engine {
         if ((v & 4) && ang)  // warp-spread angular correction: mixed SRD without beads
           cells_bps[m][v] = (mixed && !(v & (8 | 16)))
                                 ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, false, false,
-                                                           true, m, 3)
+                                                           true, m, 3, 32)
                                 : 1;
         else if ((v & 4) && !(at && (v & 1)))
           cells_bps[m][v] =
-              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, false, m, 3)
+              mixed ? cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, false, m, 3, 32)
                     : cells_warpd_blocks_per_sm((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, m);
         else if (!(v & 4))
           cells_bps[m][v] = cells_blocks_per_sm(mixed, v, m);
@@ -342,14 +347,22 @@ struct Engine {
           cells_bps[m][v] = 1;
         if (cells_bps[m][v] < 1) cells_bps[m][v] = 1;
       }
-    for (int v = 0; v < NVAR; ++v)
+    for (int v = 0; v < NVAR; ++v) {
       for (int ch = 2; ch <= 4; ++ch) {
         bps_chunk[ch][v] = cells_bps[MODE_F][v];
         if (chunk_tunable(v))
           bps_chunk[ch][v] = std::max(1, cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0,
                                                                   (v & 8) != 0, false, false,
-                                                                  MODE_F, ch));
+                                                                  MODE_F, ch, 32));
       }
+      for (int k = 0; k < 2; ++k) {
+        bps_narrow[k][v] = cells_bps[MODE_F][v];
+        if (chunk_tunable(v))
+          bps_narrow[k][v] = std::max(1, cells_warp_blocks_per_sm((v & 1) != 0, (v & 2) != 0,
+                                                                  (v & 8) != 0, false, false,
+                                                                  MODE_F, 3, k == 0 ? 16 : 8));
+      }
+    }
     CUDA_TRY((cudaError_t)md_bin_prepare());
     CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
     CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), stream));
@@ -540,13 +553,18 @@ struct Engine {
   }
 
   // Grid of the fused pass: tuned_grid 0 = the occupancy limit (blocks per
-  // SM that fit), k > 0 = at most k blocks per SM, -1 = one block per span.
+  // SM that fit), k > 0 = at most k blocks per SM, -1 = one block per span
+  // part (a 256-cell span has 32 / cells-per-warp parts).
   int tuned_grid = 0;
   int grid_of(int v, int mode) const {
-    if (mode == MODE_F && tuned_grid == -1) return std::max(n_spans[v], 1);
-    const int limit = (mode == MODE_F) ? bps_chunk[tuned_chunk][v] : cells_bps[mode][v];
+    const bool narrow = mode == MODE_F && chunk_tunable(v) && tuned_cpw != 32;
+    const int items = n_spans[v] * (narrow ? 32 / tuned_cpw : 1);
+    if (mode == MODE_F && tuned_grid == -1) return std::max(items, 1);
+    const int limit = (mode != MODE_F) ? cells_bps[mode][v]
+                      : narrow         ? bps_narrow[tuned_cpw == 16 ? 0 : 1][v]
+                                       : bps_chunk[tuned_chunk][v];
     const int bps = (mode == MODE_F && tuned_grid > 0) ? std::min(tuned_grid, limit) : limit;
-    return grid_for(n_spans[v], bps);
+    return grid_for(items, bps);
   }
 
   void launch_cells_all(int mode) {
@@ -556,7 +574,8 @@ struct Engine {
       const bool at = (v & 16) != 0;
       if ((v & 4) && mixed)
         launch_cells_warp((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, (v & 32) != 0, mode,
-                          d_boxes, d_spans[v], n_spans[v], grid, tuned_chunk, d_err, stream);
+                          d_boxes, d_spans[v], n_spans[v], grid, tuned_chunk, tuned_cpw, d_err,
+                          stream);
       else if (v & 4)
         launch_cells_warpd((v & 1) != 0, (v & 2) != 0, (v & 8) != 0, at, mode, d_boxes,
                            d_spans[v], n_spans[v], grid, d_err, stream);
@@ -640,14 +659,15 @@ struct Engine {
 
   // Launch tuner.  The paper tunes its kernels' launch parameters at run time
   // on real steps (Sec. 3.5, Sec. 4).  Here each candidate of the fused pass
-  // -- grid (1 .. occupancy-limit blocks per SM, and one block per span)
-  // times pass-2 chunk depth (2, 3, 4 windows of members in flight, for the
-  // mixed SRD variants) -- runs `reps` real steps, timed with CUDA events on
-  // the stream; the fastest is kept and the step graph re-captured.  Results
-  // do not depend on the candidate: the mixed model's cell sums are exact,
-  // the FP64 ones differ at rounding.
+  // -- grid (1 .. occupancy-limit blocks per SM, and one block per span part)
+  // times, for the mixed SRD variants, the cells per warp and pass-2 chunk
+  // depth (32 cells with 2, 3 or 4 windows of members in flight; 16 and 8
+  // cells with 3) -- runs `reps` real steps, timed with CUDA events on the
+  // stream; the fastest is kept and the step graph re-captured.  Results do
+  // not depend on the candidate: the mixed model's cell sums are exact, the
+  // FP64 ones differ at rounding.
   int tune(int64_t reps, int32_t* chosen, double* best_ms, int64_t* steps_taken,
-           int32_t* chosen_chunk) {
+           int32_t* chosen_chunk, int32_t* chosen_cpw) {
     if (reps < 1) return fail(MPCD_EINVAL, "steps per candidate < 1");
     int rc = ensure_tables();
     if (rc) return rc;
@@ -664,17 +684,26 @@ struct Engine {
     bool any_chunk = false;
     for (int v = 0; v < NVAR; ++v)
       if (n_spans[v] > 0 && chunk_tunable(v)) any_chunk = true;
-    std::vector<int> chunks = any_chunk ? std::vector<int>{2, 3, 4} : std::vector<int>{3};
+    // (cells per warp, chunk depth) pairs
+    std::vector<std::pair<int, int>> shapes;
+    if (any_chunk)
+      shapes = {{32, 2}, {32, 3}, {32, 4}, {16, 3}, {8, 3}};
+    else
+      shapes = {{32, 3}};
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     double best = 1e30;
-    int best_c = 0, best_ch = 3;
-    for (int ch : chunks) {
+    int best_c = 0, best_ch = 3, best_cpw = 32;
+    for (const auto& shape : shapes) {
+      const int ch = shape.second;
+      tuned_cpw = shape.first;
       tuned_chunk = ch;
       int maxbps = 1;
       for (int v = 0; v < NVAR; ++v)
-        if (n_spans[v] > 0) maxbps = std::max(maxbps, bps_chunk[ch][v]);
+        if (n_spans[v] > 0)
+          maxbps = std::max(maxbps, tuned_cpw == 32 ? bps_chunk[ch][v]
+                                                    : bps_narrow[tuned_cpw == 16 ? 0 : 1][v]);
       std::vector<int> cand;
       for (int k = 1; k <= maxbps; ++k) cand.push_back(k);
       cand.push_back(-1);
@@ -691,6 +720,7 @@ struct Engine {
           best = ms / (double)reps;
           best_c = c;
           best_ch = ch;
+          best_cpw = tuned_cpw;
         }
       }
     }
@@ -698,10 +728,12 @@ struct Engine {
     cudaEventDestroy(e1);
     tuned_grid = best_c;
     tuned_chunk = best_ch;
+    tuned_cpw = best_cpw;
     drop_graphs();
     CUDA_TRY(cudaGetLastError());
     if (chosen) *chosen = best_c;
     if (chosen_chunk) *chosen_chunk = best_ch;
+    if (chosen_cpw) *chosen_cpw = best_cpw;
     if (best_ms) *best_ms = best;
     if (steps_taken) *steps_taken = taken;
     return check_err();
@@ -1132,11 +1164,13 @@ int mpcd_step(mpcd_ctx* ctx, int64_t nsteps) {
 }
 
 int mpcd_tune(mpcd_ctx* ctx, int64_t steps_per_candidate, int32_t* blocks_per_sm,
-              double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk) {
+              double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk,
+              int32_t* cells_per_warp) {
   g_last_error.clear();
   if (!ctx) return fail(MPCD_EINVAL, "ctx is NULL");
   if (!ctx->box->has_state) return fail(MPCD_ESTATE, "no state set");
-  return ctx->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken, pass2_chunk);
+  return ctx->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken, pass2_chunk,
+                       cells_per_warp);
 }
 
 int mpcd_get_state(mpcd_ctx* ctx, double* pos, double* vel, double* solute_pos, double* solute_vel,
@@ -1363,10 +1397,12 @@ int mpcd_batch_step(mpcd_batch* bt, int64_t nsteps) {
 }
 
 int mpcd_batch_tune(mpcd_batch* bt, int64_t steps_per_candidate, int32_t* blocks_per_sm,
-                    double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk) {
+                    double* ms_per_step, int64_t* steps_taken, int32_t* pass2_chunk,
+                    int32_t* cells_per_warp) {
   g_last_error.clear();
   if (!bt) return fail(MPCD_EINVAL, "batch is NULL");
-  return bt->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken, pass2_chunk);
+  return bt->eng.tune(steps_per_candidate, blocks_per_sm, ms_per_step, steps_taken, pass2_chunk,
+                      cells_per_warp);
 }
 
 int mpcd_batch_get_state(mpcd_batch* bt, int32_t slot, double* pos, double* vel, uint64_t* step) {

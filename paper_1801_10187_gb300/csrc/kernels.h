@@ -29,12 +29,15 @@ constexpr int WARP_MAX_K = 448;
 // ang (mixed model, SRD without beads): the angular-momentum correction.
 // chunk: windows of 32 members whose loads and slot requests pass 2 keeps in
 // flight together (2, 3 or 4; used by the F mode of the SRD variants, 3
-// elsewhere), a launch-tuner choice.
+// elsewhere); cpw: cells per warp (8, 16 or 32; 8 and 16 only in the F mode
+// of the SRD variants, with chunks of 3, 32 elsewhere).  Both are launch-tuner
+// choices.  With cpw < 32 a 256-cell span is taken in 32 / cpw parts, each by
+// one block: grid sizes count parts.
 int cells_warp_blocks_per_sm(bool thermo, bool force, bool beads, bool at, bool ang, int mode,
-                             int chunk);
+                             int chunk, int cpw);
 void launch_cells_warp(bool thermo, bool force, bool beads, bool at, bool ang, int mode,
                        const BoxDev* boxes, const int2* spans, int nspans, int grid, int chunk,
-                       int* err, cudaStream_t s);
+                       int cpw, int* err, cudaStream_t s);
 // The FP64 model's counterpart (k_cells_warp_d.cu), same conditions.
 int cells_warpd_blocks_per_sm(bool thermo, bool force, bool beads, bool at, int mode);
 void launch_cells_warpd(bool thermo, bool force, bool beads, bool at, int mode, const BoxDev* boxes,

@@ -454,15 +454,17 @@ def test_mixed_row_capacity_limits(rho):
 
 
 def test_launch_tuner_keeps_results():
-    """mpcd_tune runs real steps under every candidate (grid x pass-2 chunk
-    depth 2, 3, 4) and keeps the fastest; the trajectory is bit-identical to
-    plain steps (mixed model)."""
+    """mpcd_tune runs real steps under every candidate (grid x cells per warp
+    and pass-2 chunk depth: 32 cells with 2, 3, 4 windows, 16 and 8 cells with
+    3) and keeps the fastest; the trajectory is bit-identical to plain steps
+    (mixed model)."""
     s = inputs.solvent((24, 24, 24), 10, seed=51, mixed=True)
     a = pkg.Box(n=(24, 24, 24), seed=51, precision="mixed", thermostat=True)
     a.set_state(s.pos, s.vel)
-    bps, ms, taken, chunk = a.tune(1)
+    bps, ms, taken, chunk, cpw = a.tune(1)
     assert bps == -1 or bps >= 1
     assert chunk in (2, 3, 4)
+    assert cpw in (8, 16, 32) and (cpw == 32 or chunk == 3)
     assert ms > 0.0 and taken >= 2
     a.step(3)
     pa, va, *_, sta = a.get_state()
@@ -475,3 +477,40 @@ def test_launch_tuner_keeps_results():
     assert sta == stb == taken + 3
     np.testing.assert_array_equal(pa, pb)
     np.testing.assert_array_equal(va, vb)
+
+
+@pytest.mark.parametrize("case", ["beads", "ragged_force"])
+def test_launch_tuner_cells_per_warp_keeps_results(case):
+    """The tuner's candidates with 16 and 8 cells per warp (a 256-cell span
+    taken in 2 or 4 parts; lanes without a cell) on the paths they change:
+    solute beads (a warp takes only its own cells' beads from the 32-cell bead
+    group) and a ragged box (23 x 17 x 9 cells, the last span part partly or
+    wholly beyond the grid) with a body force.  Every candidate advances real
+    steps; the trajectory equals plain steps bit for bit, beads included."""
+    if case == "beads":
+        n, rho, seed = (16, 16, 16), 5, 61
+        kw = dict(chain_len=10, md_substeps=5, solute_mass=5.0, bond_k=300.0, bond_r0=0.5)
+        s = inputs.solvent(n, rho, seed=seed, mixed=True)
+        sp, sv = inputs.chains(n, 40, 10, 0.5, bead_mass=5.0, seed=seed + 1)
+        box_kw = dict(thermostat=True, **kw)
+    else:
+        n, rho, seed = (23, 17, 9), 7, 62
+        s = inputs.solvent(n, rho, seed=seed, mixed=True)
+        sp = sv = None
+        box_kw = dict(thermostat=False, body_force=(0.01, -0.02, 0.005))
+    a = pkg.Box(n=n, seed=seed, precision="mixed", **box_kw)
+    a.set_state(s.pos, s.vel, sp, sv)
+    bps, ms, taken, chunk, cpw = a.tune(2)
+    assert cpw in (8, 16, 32)
+    a.step(3)
+    ra = a.get_state()
+    a.close()
+    b = pkg.Box(n=n, seed=seed, precision="mixed", **box_kw)
+    b.set_state(s.pos, s.vel, sp, sv)
+    b.step(taken + 3)
+    rb = b.get_state()
+    b.close()
+    assert ra[4] == rb[4] == taken + 3
+    for x, y in zip(ra[:4], rb[:4]):
+        if x is not None:
+            np.testing.assert_array_equal(x, y)
