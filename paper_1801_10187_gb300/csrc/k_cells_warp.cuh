@@ -86,8 +86,20 @@ struct WarpShared {
 // Thermostat variants: the exact second moment of each cell's split
 // velocities, sum over members and components of H^2, H L and L^2 (V = H 2^20
 // + L, so sum V^2 = 2^40 sum H^2 + 2^21 sum H L + sum L^2).
+//
+// A lane adds its partial P of a moment (an int64) as two 32-bit shared
+// atomics instead of one 64-bit one, P = (P >> 24) 2^24 + (P & (2^24 - 1)).
+// Both sums stay exact: a lane's share is at most 8
+// members (24 terms: |h| < 2^22, |l| <= 2^19), so |P >> 24| < 2^24.6 for H^2,
+// 2^21.6 for H L and 2^18.6 for L^2, and a cell of at most 448 members takes at
+// most 4 staged blocks of 32 lane shares, 128 partials: the high sums stay
+// below 2^32 (H^2, unsigned) and 2^29 in magnitude (the others), the low sums
+// below 2^31.
 struct ThermoShared {
-  unsigned long long hh[32], hl[32], ll[32];
+  unsigned hh_lo[32], hh_hi[32];
+  unsigned hl_lo[32];
+  int hl_hi[32];
+  unsigned ll_lo[32], ll_hi[32];
 };
 
 // Per-cell bead accumulators of one warp (bead variants only): exact int64
@@ -445,9 +457,12 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
         }
       }
       if (THERMO) {
-        TS.hh[lane] = 0ull;
-        TS.hl[lane] = 0ull;
-        TS.ll[lane] = 0ull;
+        TS.hh_lo[lane] = 0u;
+        TS.hh_hi[lane] = 0u;
+        TS.hl_lo[lane] = 0u;
+        TS.hl_hi[lane] = 0;
+        TS.ll_lo[lane] = 0u;
+        TS.ll_hi[lane] = 0u;
       }
       __syncwarp();
       bool slow = false, slow_d = false;
@@ -526,9 +541,12 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
           }
           if (last) {
             if (THERMO) {
-              atomicAdd(&TS.hh[o], (unsigned long long)Shh);
-              atomicAdd(&TS.hl[o], (unsigned long long)Shl);
-              atomicAdd(&TS.ll[o], (unsigned long long)Sll);
+              atomicAdd(&TS.hh_lo[o], (unsigned)(Shh & 0xFFFFFFLL));
+              atomicAdd(&TS.hh_hi[o], (unsigned)(Shh >> 24));
+              atomicAdd(&TS.hl_lo[o], (unsigned)(Shl & 0xFFFFFFLL));
+              atomicAdd(&TS.hl_hi[o], (int)(Shl >> 24));
+              atomicAdd(&TS.ll_lo[o], (unsigned)(Sll & 0xFFFFFFLL));
+              atomicAdd(&TS.ll_hi[o], (unsigned)(Sll >> 24));
               Shh = 0;
               Shl = 0;
               Sll = 0;
@@ -673,8 +691,9 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
           Qt[q] = exact64 ? Q[q] : (long long)W.h[q][lane] * 1048576LL + (long long)W.l[q][lane] + Q[q];
         const __int128 S2 =
             exact64 ? S2x
-                    : ((__int128)(long long)TS.hh[lane] << 40) +
-                          ((__int128)(long long)TS.hl[lane] << 21) + (__int128)(long long)TS.ll[lane] +
+                    : ((__int128)(((long long)TS.hh_hi[lane] << 24) + TS.hh_lo[lane]) << 40) +
+                          ((__int128)((long long)TS.hl_hi[lane] * 16777216LL + TS.hl_lo[lane]) << 21) +
+                          (__int128)(((long long)TS.ll_hi[lane] << 24) + TS.ll_lo[lane]) +
                           S2x;
         const long long Kx = (BEADS && gnb > 0) ? (long long)BS.E[lane] : 0ll;
         double Mt;
