@@ -40,6 +40,32 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def declared_arity():
+    """Number of parameters of each function the header declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    out = {}
+    for m in re.finditer(r"\b(mpcd_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", text):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header(lib):
+    """Every function the binding gives argument types to takes as many
+    arguments as the header declares (a stale binding would pass garbage)."""
+    arity = declared_arity()
+    assert "mpcd_tune" in arity and arity["mpcd_tune"] == 7
+    checked = 0
+    for name, n in arity.items():
+        fn = getattr(lib, name)
+        if fn.argtypes is not None:
+            assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+            checked += 1
+    assert checked >= 20
+
+
 def _c_layout(struct, fields, tmp_path):
     prog = tmp_path / "layout.c"
     lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void){",
