@@ -269,6 +269,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jobs", type=int, default=None, help="served workload: number of jobs")
     ap.add_argument("--no-sweep", action="store_true", help="served workload: skip the rate sweep")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the launch tuner: the engine's default launch (blocks per SM at "
+                         "the occupancy limit, pass-2 chunks of 3, 32 cells per warp); for "
+                         "profiling a fixed configuration")
     args = ap.parse_args()
     cfg = workload_cfg(args.workload)
     kind = cfg.get("kind", "box")
@@ -326,10 +330,14 @@ def main():
     box.step(W)
     # launch tuner on real warm-up steps (grid of the fused pass), then the
     # re-captured step graph warms up again
-    tuned_bps, tuned_ms, _, tuned_chunk, tuned_cpw = box.tune(2)
-    config["launch"] = {"blocks_per_sm": tuned_bps if tuned_bps > 0 else "one per span part",
-                        "pass2_chunk": tuned_chunk, "cells_per_warp": tuned_cpw,
-                        "tuner_ms_per_step": tuned_ms}
+    if args.no_tune:
+        config["launch"] = {"blocks_per_sm": "occupancy limit", "pass2_chunk": 3,
+                            "cells_per_warp": 32, "tuner": "off"}
+    else:
+        tuned_bps, tuned_ms, _, tuned_chunk, tuned_cpw = box.tune(2)
+        config["launch"] = {"blocks_per_sm": tuned_bps if tuned_bps > 0 else "one per span part",
+                            "pass2_chunk": tuned_chunk, "cells_per_warp": tuned_cpw,
+                            "tuner_ms_per_step": tuned_ms}
     box.step(2)
     torch.cuda.synchronize()
 

@@ -65,6 +65,14 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// Exact int64 momentum and kinetic-energy sums of the beads in each of a
+// warp's cells (bead variants), kept in the staging buffer during the cell
+// phase (see BeadShared).
+struct BeadSums {
+  unsigned long long X[3][32];
+  unsigned long long E[32];
+};
+
 // CH: windows of 32 members per chunk of pass 2 (the launch tuner picks 2, 3
 // or 4 for the F mode of the SRD variants; 3 elsewhere).
 template <int CH>
@@ -79,6 +87,7 @@ struct WarpShared {
   union {
     float sv[3][STAGE_PAD];        // pass 1: staged velocities (index j + j / 32)
     float4 sv4[STAGE4];            // pass 1 of the SRD variants: staged (v, tag)
+    BeadSums bx;                   // cell phase (bead variants): the beads' exact sums
     float4 buf[CH][2][32];         // pass 2: records of one chunk (two halves)
   };
 };
@@ -102,11 +111,11 @@ struct ThermoShared {
   unsigned ll_lo[32], ll_hi[32];
 };
 
-// Per-cell bead accumulators of one warp (bead variants only): exact int64
-// momentum and kinetic-energy sums and the bead count of each of the 32 cells.
+// Per-cell bead accumulators of one warp (bead variants only): the bead count
+// of each of the 32 cells (before the draws, which need it), and their exact
+// int64 momentum and kinetic-energy sums (after pass 1, in the staging
+// buffer, which pass 1 no longer needs and pass 2 has not yet taken).
 struct BeadShared {
-  unsigned long long X[3][32];
-  unsigned long long E[32];
   int nb[32];
 };
 
@@ -179,8 +188,11 @@ __host__ __device__ constexpr size_t block_smem(bool beads, bool at, bool ang = 
 
 }  // namespace
 
-// Thermostat and bead variants keep more values live through the per-cell
-// phase; they run three blocks per SM with 80 registers instead of spilling.
+// The SRD variants run four blocks per SM (64 registers); the thermostat
+// variants then spill about 50 bytes, which costs less than the fourth block
+// gains (measured).  With the beads' sums in the staging buffer during the
+// cell phase, four blocks of the thermostat and bead variant fit in shared
+// memory.
 // AT selects the Andersen rule (then THERMO is false): its two Box-Muller
 // draws per member want registers for independent chains, and its cache of
 // random velocities wants shared memory, so it runs two blocks per SM.
@@ -194,7 +206,7 @@ __host__ __device__ constexpr size_t block_smem(bool beads, bool at, bool ang = 
 // blocks per SM.
 template <bool THERMO, int MODE, bool FORCE, bool BEADS, bool AT, bool ANG, int CH = CHUNK,
           int CPW = 32>
-__global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 3 : 4)) k_cells_warp(const BoxDev* __restrict__ boxes,
+__global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : 4) k_cells_warp(const BoxDev* __restrict__ boxes,
                                                          const int2* __restrict__ spans,
                                                          int nspans, int* err) {
   using R = RecF;
@@ -407,21 +419,9 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
     };
     if (BEADS && MODE != MODE_P) {
       if (gnb > 0) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) BS.X[q][lane] = 0ull;
-        BS.E[lane] = 0ull;
         BS.nb[lane] = 0;
         __syncwarp();
-        for_beads([&](int j, int lc) {
-          const double w0 = B.bgv[3 * j], w1 = B.bgv[3 * j + 1], w2 = B.bgv[3 * j + 2];
-          atomicAdd(&BS.X[0][lc], (unsigned long long)__double2ll_rn((B.Mb * w0) * 4294967296.0));
-          atomicAdd(&BS.X[1][lc], (unsigned long long)__double2ll_rn((B.Mb * w1) * 4294967296.0));
-          atomicAdd(&BS.X[2][lc], (unsigned long long)__double2ll_rn((B.Mb * w2) * 4294967296.0));
-          if (THERMO)  // kinetic term of the one-pass energy (Sec. 3.5)
-            atomicAdd(&BS.E[lc], (unsigned long long)__double2ll_rn(
-                                     (B.Mb * (w0 * w0 + w1 * w1 + w2 * w2)) * 4294967296.0));
-          atomicAdd(&BS.nb[lc], 1);
-        });
+        for_beads([&](int, int lc) { atomicAdd(&BS.nb[lc], 1); });
         __syncwarp();
         nb = BS.nb[lane];
       }
@@ -577,12 +577,29 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
       const bool exact64 = __any_sync(FULL, slow);  // a velocity of 1024 or more
       const bool exact64_d = AT && __any_sync(FULL, slow_d);
 
-      // ---- per cell: u (Sec. 3.5), then E_k and xi ----
+      // the beads' exact momentum and (with the thermostat) kinetic sums per
+      // cell, into the staging buffer that pass 1 is done with
       long long X[3] = {0, 0, 0};
       if (BEADS && gnb > 0) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) X[q] = (long long)BS.X[q][lane];
+        for (int q = 0; q < 3; ++q) W.bx.X[q][lane] = 0ull;
+        W.bx.E[lane] = 0ull;
+        __syncwarp();
+        for_beads([&](int j, int lc) {
+          const double w0 = B.bgv[3 * j], w1 = B.bgv[3 * j + 1], w2 = B.bgv[3 * j + 2];
+          atomicAdd(&W.bx.X[0][lc], (unsigned long long)__double2ll_rn((B.Mb * w0) * 4294967296.0));
+          atomicAdd(&W.bx.X[1][lc], (unsigned long long)__double2ll_rn((B.Mb * w1) * 4294967296.0));
+          atomicAdd(&W.bx.X[2][lc], (unsigned long long)__double2ll_rn((B.Mb * w2) * 4294967296.0));
+          if (THERMO)  // kinetic term of the one-pass energy (Sec. 3.5)
+            atomicAdd(&W.bx.E[lc], (unsigned long long)__double2ll_rn(
+                                       (B.Mb * (w0 * w0 + w1 * w1 + w2 * w2)) * 4294967296.0));
+        });
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 3; ++q) X[q] = (long long)W.bx.X[q][lane];
       }
+
+      // ---- per cell: u (Sec. 3.5), then E_k and xi ----
       const bool occupied = n > 0 || nb > 0;
       float u[3] = {0.0f, 0.0f, 0.0f};
       long long Q[3] = {0, 0, 0};  // exact path: this cell's sums of rne(v 2^32)
@@ -695,7 +712,7 @@ __global__ void __launch_bounds__(BLOCK, (AT || ANG) ? 2 : ((THERMO || BEADS) ? 
                           ((__int128)((long long)TS.hl_hi[lane] * 16777216LL + TS.hl_lo[lane]) << 21) +
                           (__int128)(((long long)TS.ll_hi[lane] << 24) + TS.ll_lo[lane]) +
                           S2x;
-        const long long Kx = (BEADS && gnb > 0) ? (long long)BS.E[lane] : 0ll;
+        const long long Kx = (BEADS && gnb > 0) ? (long long)W.bx.E[lane] : 0ll;
         double Mt;
         const double Ep = mixed_ek_mt(B, (int)n, nb, 0, Qt, S2, X, Kx, Mt);
         const float2 dv = W.gdv[lane];
