@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -229,11 +230,20 @@ def kernel_traffic(kernel, workload):
     return ent["dram_bytes_per_launch"] * ent.get("scale_to_workload", 1.0)
 
 
+def _code_only(text):
+    """Source text without comments and blank lines: what the compiled kernel
+    depends on (an edit of a comment does not change the counters)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def sources_hash(paths):
     h = hashlib.sha256()
     for rel in paths:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
 
 

@@ -1,31 +1,37 @@
 // k_cells_warp.cuh -- the fused SRD step of the mixed model with the members of
-// 32 cells spread over the 32 lanes of a warp (arXiv:1801.10187: Sec. 2 Eqs.
+// a warp's cells spread over its 32 lanes (arXiv:1801.10187: Sec. 2 Eqs.
 // stream, srd and thermo; Sec. 3.4 cell list; Sec. 3.5 cell properties;
 // Sec. 3.6 rotation and thermostat, algorithm "SRD collision rule").
 //
 // Same modes, records and results as k_cells (one thread per cell), for boxes
-// without walls (solute beads allowed).  A warp owns 32 consecutive cells.  Their row
-// members are numbered 0 .. N-1 in cell order (a warp prefix sum of the row
-// counts); a byte map gives each member's cell.
-//   pass 1   the velocities of up to 256 members are read in member order
-//            (neighbouring lanes read neighbouring records) into shared
-//            memory; then lane j takes a consecutive share of them, so its
-//            members lie in one or two cells.  Each velocity component gives
-//            rne(v 2^32) = H 2^20 + L, two int32 parts from two magic-number
-//            roundings, summed in registers while the cell stays the same
-//            and added to the cell's shared sums by one atomic per part when
-//            it changes.  The sums are exact, so u is the one of any order.
+// without walls (solute beads allowed).  A warp owns 32 consecutive cells (or
+// 16 or 8, a launch-tuner choice; see CPW below).  Their row members are
+// numbered 0 .. N-1 in cell order (a warp prefix sum of the row counts); a
+// byte map gives each member's cell.
+//   pass 1   the (v, tag) words of up to 192 members are copied into shared
+//            memory asynchronously in member order (neighbouring lanes,
+//            neighbouring records), issued as soon as the counts are scanned
+//            so that they land while the bead counts and the per-cell draws
+//            compute (the Andersen and angular variants load up to 256
+//            velocities in windows of registers instead); then lane j takes a
+//            consecutive share of them, so its members lie in one or two
+//            cells.  Each velocity component gives rne(v 2^32) = H 2^20 + L,
+//            two int32 parts from two magic-number roundings, summed in
+//            registers while the cell stays the same and added to the cell's
+//            shared sums by one atomic per part when it changes.  The sums
+//            are exact, so u is the one of any order.
 //   cell     lane c turns the sums of cell c into u and, with the thermostat,
 //            into E_k (one pass, Sec. 3.5: pass 1 also sums the exact second
 //            moment of the split velocities) and the factor xi; the axis and
 //            the Gamma pair were drawn before pass 1 (they need only the
 //            member count).  u, xi and the axis go to shared memory
-//   pass 2   members in order across the lanes, in chunks of three windows:
-//            the chunk's records are copied into shared memory asynchronously
-//            (all in flight at once), each is collided with its cell's
-//            parameters, streamed and binned under the next shift while its
-//            slot in the new row is requested (atomic on the row count), and
-//            the records are written once every request of the chunk is out
+//   pass 2   members in order across the lanes, in chunks of two to four
+//            windows of 32: the chunk's records are copied into shared memory
+//            asynchronously (all in flight at once), each is collided with its
+//            cell's parameters, streamed and binned under the next shift while
+//            its slot in the new row is requested (atomic on the row count),
+//            and the records are written once every request of the chunk is
+//            out
 // The parameters a member needs (time step, box, rotation, the thresholds of
 // the next grid shift, row pointers) are staged in shared memory when a block
 // meets a new box.  Members beyond the row capacity (overflow list) stay with the lane
