@@ -35,3 +35,21 @@ def test_profile_summaries_give_their_commands():
             text = f.read()
         assert "ncu " in text and "--clock-control none" in text, name
         assert "python bench.py" in text, name
+
+
+def test_sources_hash_follows_code_not_comments(tmp_path, monkeypatch):
+    """The record's hash changes with the code and not with comments or blank
+    lines (the counters depend on the compiled code only)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    src = tmp_path / "k.cu"
+    src.write_text("// a kernel\n__global__ void k(int* x) {\n  x[0] = 1;  /* one */\n}\n")
+    h0 = bench.sources_hash(["k.cu"])
+    src.write_text("/* another\n   comment */\n__global__ void k(int* x) {\n\n  x[0] = 1;  // one\n}\n")
+    assert bench.sources_hash(["k.cu"]) == h0
+    src.write_text("__global__ void k(int* x) {\n  x[0] = 2;\n}\n")
+    assert bench.sources_hash(["k.cu"]) != h0
+
